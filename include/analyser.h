@@ -1,0 +1,238 @@
+/*
+ * analyser.h -- C ABI of the GB300 video analyser (shot boundaries, sampling
+ * structure, dynamic keyframes) of arXiv 2502.09202.
+ *
+ * The library computes the paper's per-frame measures on the GPU and runs its
+ * detectors on the host:
+ *   AMM(I,J)  average magnitude of the motion field between I and J   (Sec. III.A)
+ *   SWR(I,J)  dissimilarity 1 - NCC of I and motion-compensated J      (Sec. III.A)
+ *   ACT(I,J)  geometric mean sqrt(AMM * SWR)                           (Sec. III.A)
+ *   ACT(I_t, I_t+1) for every t; every other measure on demand          (Sec. III.A)
+ *   shot boundaries: fast check, then a deep check for K = 1..Kmax      (Sec. III.B)
+ *   sampling structure from v0 = ACT(u_t,l_t), v1 = ACT(u_t,l_t+1),
+ *     v2 = ACT(l_t,u_t+1), field order from beta = v1/v2                (Sec. III.C)
+ *   dynamic keyframes by accumulated activity                           (Sec. III.D)
+ *
+ * Conventions for every call:
+ *   - plain C types; every call that can fail returns an int status
+ *     (ANALYSER_OK or a negative error code) and never throws or aborts;
+ *   - errors are sticky per handle: after a failure the handle refuses further
+ *     work with the same code (analyser_last_error reports it);
+ *   - frames are 8-bit luma planes, row-major, `pitch_bytes` between rows;
+ *   - "device" pointers are CUDA device pointers of the current device.
+ */
+#ifndef GB300_VIDEO_ANALYSER_H
+#define GB300_VIDEO_ANALYSER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------- */
+#define ANALYSER_OK 0
+#define ANALYSER_ERR_INVALID_ARG (-1) /* null pointer, bad size/pitch, unsupported parameters */
+#define ANALYSER_ERR_OOM (-2)         /* device or host allocation failed, or budget exceeded */
+#define ANALYSER_ERR_CUDA (-3)        /* a CUDA call failed (the message says which) */
+#define ANALYSER_ERR_TIMEOUT (-4)     /* a bounded device wait gave up */
+#define ANALYSER_ERR_STATE (-5)       /* call not allowed in this state (e.g. push after finish) */
+#define ANALYSER_PENDING 1            /* server_poll: the request is not done yet */
+
+/* ---- labels ---------------------------------------------------------------- */
+#define ANALYSER_UNKNOWN 0
+#define ANALYSER_PROGRESSIVE 1
+#define ANALYSER_INTERLACED 2
+#define ANALYSER_PULLDOWN 3
+#define ANALYSER_FO_NONE 0
+#define ANALYSER_FO_TFF 1 /* upper (even-row) field first */
+#define ANALYSER_FO_BFF 2 /* lower (odd-row) field first */
+
+/* ---- pair kinds of a measure record ----------------------------------------- */
+#define ANALYSER_PAIR_FRAME 0       /* I = frame a, J = frame b */
+#define ANALYSER_PAIR_UPPER_LOWER 1 /* I = upper field of a, J = lower field of b */
+#define ANALYSER_PAIR_LOWER_UPPER 2 /* I = lower field of a, J = upper field of b */
+
+/*
+ * Parameters.  The paper fixes none of the motion estimator's choices and none
+ * of the thresholds (Sec. III); these defaults are the readings the library and
+ * its tests use.  Fill with analyser_default_params() and change fields.
+ */
+typedef struct {
+  /* motion estimator: integer block matching on a box-filter pyramid */
+  int block;           /* level-0 block side B0 = 4 << (levels-1)          (16) */
+  int levels;          /* pyramid depth L, 2 or 3                           (3) */
+  int radius_coarse;   /* exhaustive radius R at the coarsest level: 8, 16, 24 (16) */
+  int radius_refine;   /* refinement radius r at finer levels, 0..4          (2) */
+  int mv_cost;         /* lambda: cost per pixel of |vx|+|vy| added to the SAD, 0..64 (4) */
+  /* shot detector (Sec. III.B) */
+  int kmax;            /* largest dissolve span K tested, 1..16              (8) */
+  int jback;           /* J: predecessors compared in the deep check, and needed
+                          in the shot before a fast check                    (2) */
+  int fast_window;     /* median window W                                    (8) */
+  double fast_lambda;  /* candidate iff a_t > max(fast_tau, fast_lambda*median) (2.0) */
+  double fast_rise;    /* ... or a_t > max(fast_tau, fast_rise*median) and a_t < a_t+1 < a_t+2 (1.3) */
+  double fast_tau;     /*                                                    (0.5) */
+  double deep_rho;     /* x << y  iff  deep_rho*x + deep_tau < y             (2.0) */
+  double deep_tau;     /*                                                    (0.5) */
+  /* sampling structure (Sec. III.C) */
+  int samp_max_frames;   /* frames analysed per shot                          (20) */
+  double static_amm_px;  /* frames with AMM(t,t+1) below this are skipped     (0.5) */
+  double comb_ratio;     /* combed iff v0 > comb_ratio * max(v1,v2)            (0.3) */
+  double unequal_ratio;  /* interlaced needs median(v1/v2) > this or < 1/this (1.12) */
+  double pulldown_match; /* fraction of frames matching the 3:2 comb pattern  (0.8) */
+  /* dynamic keyframes (Sec. III.D) */
+  double kf_theta;       /* keyframe when the accumulated activity exceeds this (8.0) */
+  /* resources */
+  int device;                          /* CUDA device ordinal                 (0) */
+  int window_frames;                   /* rolling window of frames on the device (0 = auto) */
+  unsigned long long mem_budget_bytes; /* device memory cap for one analyser (0 = none) */
+  int want_motion;                     /* keep level-0 motion fields of frame pairs (t,t+1) (0) */
+  int tile_x, tile_y;                  /* pair-kernel tile in blocks (8x4, 4x4, 8x2, 16x2, 4x8);
+                                          0 = autotuned per resolution (0, 0) */
+} analyser_params;
+
+/* One measure of one pair, in the order of (kind, a, b). */
+typedef struct {
+  int kind, a, b;
+  int64_t si, sj, sii, sjj, sij; /* exact sums of i, j, i^2, j^2, i*j over the pair's pixels */
+  int64_t sabs;                  /* residual: sum of |i - j| (J motion-compensated) */
+  int64_t samm;                  /* sum over blocks of floor(|v| * 65536) */
+  int64_t n, nb;                 /* pixels and blocks of the pair */
+  double ncc, swr, amm, act;
+} analyser_measure;
+
+typedef struct {
+  int first, last;     /* frame range of the shot (inclusive) */
+  int label;           /* ANALYSER_UNKNOWN / _PROGRESSIVE / _INTERLACED / _PULLDOWN */
+  int field_order;     /* ANALYSER_FO_* (interlaced shots) */
+  int pulldown_phase;  /* 0..4: a frame t with (t - phase) mod 5 == 0 shows fields A A; -1 if none */
+  int analysed;        /* frames that voted */
+} analyser_shot;
+
+typedef struct {
+  int nframes;
+  int ncuts;      const int* cuts;            /* first frame of each new shot after a hardcut */
+  int ndissolves; const int* dissolves;       /* pairs (t, K): last frame before, span */
+  int nshots;     const analyser_shot* shots;
+  int label, field_order, pulldown_phase;     /* clip-level verdict */
+  int nkeyframes; const int* keyframes;
+  int nmeasures;  const analyser_measure* measures;
+  int motion_w, motion_h;                     /* block grid of the motion dumps (0 if none) */
+  const int16_t* motion;                      /* (nframes-1) x motion_h x motion_w x 2 (vx, vy), or null */
+} analyser_results_t;
+
+typedef struct analyser analyser;
+typedef struct server server;
+
+/* Defaults of every parameter (values in the comments above). */
+int analyser_default_params(analyser_params* p);
+
+/*
+ * Create an analyser for a clip of width x height luma frames at `fps` frames/s.
+ * Requirements: 64 <= width, 64 <= height, height even, width*height <= 11,800,000
+ * (exact 64-bit correlation sums), parameters within the ranges above.
+ * On success *out owns the device buffers of the rolling frame window.
+ */
+int analyser_create(int width, int height, double fps, const analyser_params* p, analyser** out);
+
+/*
+ * Append `nframes` frames from HOST memory (frame k at luma + k*height*pitch_bytes,
+ * rows pitch_bytes apart, pitch_bytes >= width).  The frames are copied; the
+ * caller keeps ownership.  Runs GPU work as the window fills; returns when all
+ * frames are copied.  Error ANALYSER_ERR_STATE after analyser_finish.
+ */
+int analyser_push_frames(analyser* a, const uint8_t* luma, long long pitch_bytes, int nframes);
+
+/*
+ * Append `nframes` frames already resident in DEVICE memory (frame k at
+ * luma + k*frame_stride_bytes; pitch_bytes a multiple of 16, luma 16-byte
+ * aligned).  No copy is made: the buffer must stay valid and unchanged until
+ * analyser_finish returns.
+ */
+int analyser_push_frames_device(analyser* a, const uint8_t* luma, long long pitch_bytes,
+                                long long frame_stride_bytes, int nframes);
+
+/* No more frames: runs the remaining work to the end of the clip. */
+int analyser_finish(analyser* a);
+
+/*
+ * Results after analyser_finish.  Pointers are owned by the analyser and stay
+ * valid until the next call on it or analyser_destroy.
+ */
+int analyser_results(analyser* a, analyser_results_t* out);
+
+/* Last error code and a one-line message (owned by the analyser). */
+int analyser_last_error(const analyser* a, const char** message);
+
+/* Counters of the last run: pair measures computed, GPU waves, kernel launches. */
+int analyser_stats(const analyser* a, long long* pairs, long long* waves, long long* launches);
+
+void analyser_destroy(analyser* a);
+
+/*
+ * Stateless measure of `npairs` pairs on DEVICE frames, for tests and kernel
+ * timing: pair k compares frame ia[k] with frame ib[k] of `frames` (frame f at
+ * frames + f*frame_stride_bytes) with pair kind kinds[k].  records receives
+ * 7 int64 per pair (sum i, sum j, sum i^2, sum j^2, sum i*j, sum |i-j|, S_amm)
+ * in HOST memory; motion (optional, HOST) receives the level-0 field of every
+ * pair, nby*nbx (vx, vy) int16 each.  `stream` is a cudaStream_t (0 = default).
+ * Allocates its pyramids and queues on the device for the duration of the call.
+ */
+int analyser_measure_pairs(const analyser_params* p, int width, int height, const uint8_t* frames,
+                           long long pitch_bytes, long long frame_stride_bytes, int nframes,
+                           const int* kinds, const int* ia, const int* ib, int npairs,
+                           int64_t* records, int16_t* motion, void* stream);
+
+/*
+ * Host-only: run the detectors alone on measures supplied by `get`, without a
+ * GPU.  get(ctx, kind, a, b, rec) fills rec[0..8] = sum i, sum j, sum i^2,
+ * sum j^2, sum i*j, sum |i-j|, S_amm, n, nb for pair (kind, a, b) and returns 0
+ * (nonzero aborts with ANALYSER_ERR_INVALID_ARG).  The FP64 finalisation and
+ * every decision are the library's own.  *out is an analyser handle whose only
+ * valid calls are analyser_results, analyser_last_error and analyser_destroy.
+ */
+typedef int (*analyser_measure_fn)(void* ctx, int kind, int a, int b, int64_t* rec);
+int analyser_detect_offline(const analyser_params* p, int width, int height, int nframes,
+                            analyser_measure_fn get, void* ctx, analyser** out);
+
+/* ---- serving: continuous batching of many clips on one GPU ------------------- */
+
+/* A server admits clips while the device-memory budget allows. */
+int server_create(const analyser_params* p, unsigned long long budget_bytes, server** out);
+
+/*
+ * Submit a whole clip from HOST memory (copied before return is NOT guaranteed:
+ * the buffer must stay valid until server_poll reports the ticket done).
+ * *ticket identifies the request.
+ */
+int server_submit(server* s, int width, int height, double fps, const uint8_t* frames,
+                  long long pitch_bytes, int nframes, long long* ticket);
+
+/* ANALYSER_PENDING while the clip is queued or running; ANALYSER_OK with the
+ * results (owned by the server, valid until server_release or destroy). */
+int server_poll(server* s, long long ticket, analyser_results_t* out);
+
+/*
+ * One scheduling step: admit queued clips while the budget allows, copy the
+ * next frames of every admitted clip into its window, run one GPU wave over
+ * all of them and retire finished clips.  *active (optional) receives the
+ * number of clips admitted or queued after the step.
+ */
+int server_step(server* s, int* active);
+
+/* Run server_step until every submitted clip is done. */
+int server_drain(server* s);
+
+/* Per-request timing: seconds from submit to results ready. */
+int server_latency(const server* s, long long ticket, double* seconds);
+
+/* Free one finished request's results. */
+int server_release(server* s, long long ticket);
+
+void server_destroy(server* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_VIDEO_ANALYSER_H */

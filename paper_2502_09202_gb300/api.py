@@ -1,0 +1,249 @@
+"""Python face of the C ABI: Analyser, Server, measure_pairs, detect_offline.
+
+Every computation runs in the CUDA library; this module converts arguments and
+results.  PyTorch is used only to hand over device buffers and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import native as N
+from .native import AnalyserError, default_params
+
+__all__ = ["Analyser", "Server", "measure_pairs", "detect_offline", "default_params", "AnalyserError",
+           "results_to_dict"]
+
+
+def _check(code: int, where: str, handle=None):
+    if code not in (N.OK, N.PENDING):
+        msg = ""
+        if handle is not None and where.startswith("analyser"):
+            m = ctypes.c_char_p()
+            N.lib.analyser_last_error(handle, ctypes.byref(m))
+            msg = (m.value or b"").decode(errors="replace")
+        raise AnalyserError(code, where, msg)
+    return code
+
+
+def results_to_dict(r: N.Results) -> dict:
+    """Results in the layout the oracle returns (measures keyed by (kind, a, b))."""
+    cuts = [r.cuts[i] for i in range(r.ncuts)]
+    dis = [(r.dissolves[2 * i], r.dissolves[2 * i + 1]) for i in range(r.ndissolves)]
+    shots = [{"first": s.first, "last": s.last, "label": s.label, "field_order": s.field_order,
+              "phase": s.pulldown_phase, "analysed": s.analysed} for s in (r.shots[i] for i in range(r.nshots))]
+    kf = [r.keyframes[i] for i in range(r.nkeyframes)]
+    meas = {}
+    for i in range(r.nmeasures):
+        m = r.measures[i]
+        meas[(m.kind, m.a, m.b)] = {"si": m.si, "sj": m.sj, "sii": m.sii, "sjj": m.sjj, "sij": m.sij,
+                                    "sabs": m.sabs, "samm": m.samm, "n": m.n, "nb": m.nb,
+                                    "ncc": m.ncc, "swr": m.swr, "amm": m.amm, "act": m.act}
+    out = {"cuts": cuts, "dissolves": dis, "keyframes": kf, "shots": shots, "label": r.label,
+           "field_order": r.field_order, "pulldown_phase": r.pulldown_phase, "measures": meas,
+           "nframes": r.nframes}
+    if r.motion:
+        n = max(r.nframes - 1, 0) * r.motion_h * r.motion_w * 2
+        out["motion"] = np.ctypeslib.as_array(r.motion, shape=(n,)).reshape(-1, r.motion_h, r.motion_w, 2).copy()
+    return out
+
+
+class Analyser:
+    """One clip: create, push frames (host or device), finish, results."""
+
+    def __init__(self, width: int, height: int, fps: float = 25.0, params: N.Params | None = None, **overrides):
+        self.params = params if params is not None else default_params(**overrides)
+        self._h = ctypes.c_void_p()
+        _check(N.lib.analyser_create(width, height, float(fps), ctypes.byref(self.params), ctypes.byref(self._h)),
+               "analyser_create")
+        self.width, self.height = width, height
+        self._keep = []          # device buffers referenced by push_device
+
+    def push(self, frames: np.ndarray):
+        """Host frames: uint8 array (n, height, width) or (height, width)."""
+        f = np.ascontiguousarray(frames, dtype=np.uint8)
+        if f.ndim == 2:
+            f = f[None]
+        assert f.shape[1:] == (self.height, self.width), f.shape
+        _check(N.lib.analyser_push_frames(self._h, f.ctypes.data, f.shape[2], f.shape[0]), "analyser_push_frames",
+               self._h)
+
+    def push_host_ptr(self, ptr: int, pitch: int, n: int):
+        _check(N.lib.analyser_push_frames(self._h, ptr, pitch, n), "analyser_push_frames", self._h)
+
+    def push_device(self, frames):
+        """Device frames: a CUDA uint8 torch tensor (n, height, pitch>=width) kept alive until finish()."""
+        assert frames.is_cuda and frames.dtype.itemsize == 1 and frames.dim() == 3
+        pitch = frames.stride(1)
+        stride = frames.stride(0)
+        assert frames.stride(2) == 1
+        self._keep.append(frames)
+        _check(N.lib.analyser_push_frames_device(self._h, frames.data_ptr(), pitch, stride, frames.shape[0]),
+               "analyser_push_frames_device", self._h)
+
+    def finish(self):
+        _check(N.lib.analyser_finish(self._h), "analyser_finish", self._h)
+
+    def results(self) -> dict:
+        r = N.Results()
+        _check(N.lib.analyser_results(self._h, ctypes.byref(r)), "analyser_results", self._h)
+        return results_to_dict(r)
+
+    def stats(self) -> dict:
+        p, w, l = N.c_ll(), N.c_ll(), N.c_ll()
+        N.lib.analyser_stats(self._h, ctypes.byref(p), ctypes.byref(w), ctypes.byref(l))
+        return {"pairs": p.value, "waves": w.value, "launches": l.value}
+
+    def close(self):
+        if self._h:
+            N.lib.analyser_destroy(self._h)
+            self._h = ctypes.c_void_p()
+        self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def analyse(frames: np.ndarray, fps: float = 25.0, **overrides) -> dict:
+    """Whole-clip convenience: host frames in, results out."""
+    n, h, w = frames.shape
+    with Analyser(w, h, fps, **overrides) as a:
+        a.push(frames)
+        a.finish()
+        return a.results()
+
+
+def measure_pairs(frames, kinds, ia, ib, params: N.Params | None = None, want_motion: bool = False,
+                  stream=None, **overrides):
+    """Stateless measures of pairs of DEVICE frames: a CUDA uint8 tensor (n, h, w) whose rows
+    may be padded (a view frames[:, :, :w] of a wider buffer; row pitch = stride(1)).
+
+    Returns (records int64 (npairs, 7), motion int16 list or None)."""
+    import torch
+    assert frames.is_cuda and frames.dim() == 3 and frames.stride(2) == 1
+    p = params if params is not None else default_params(**overrides)
+    n, h, w = frames.shape[0], frames.shape[1], frames.shape[2]
+    kinds = np.ascontiguousarray(kinds, dtype=np.int32)
+    ia = np.ascontiguousarray(ia, dtype=np.int32)
+    ib = np.ascontiguousarray(ib, dtype=np.int32)
+    npairs = len(kinds)
+    rec = np.zeros((npairs, 7), np.int64)
+    B0 = p.block
+    mot = None
+    mot_ptr = None
+    if want_motion:
+        sizes = [(w // B0) * ((h if k == 0 else h // 2) // B0) * 2 for k in kinds]
+        mot = np.zeros(sum(sizes), np.int16)
+        mot_ptr = mot.ctypes.data_as(ctypes.POINTER(ctypes.c_int16))
+    st = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    code = N.lib.analyser_measure_pairs(
+        ctypes.byref(p), w, h, frames.data_ptr(), frames.stride(1), frames.stride(0), n,
+        kinds.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ia.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+        ib.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), npairs, rec.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+        mot_ptr, ctypes.c_void_p(st))
+    _check(code, "analyser_measure_pairs")
+    if want_motion:
+        out, off = [], 0
+        for k in kinds:
+            hh = h if k == 0 else h // 2
+            m = (w // B0) * (hh // B0) * 2
+            out.append(mot[off:off + m].reshape(hh // B0, w // B0, 2))
+            off += m
+        return rec, out
+    return rec, None
+
+
+def detect_offline(width: int, height: int, nframes: int, get_record, params: N.Params | None = None,
+                   **overrides) -> dict:
+    """Run the library's detectors (host only, no GPU) on records from ``get_record(kind, a, b)``,
+    which returns the 9 integers (si, sj, sii, sjj, sij, sabs, samm, n, nb)."""
+    p = params if params is not None else default_params(**overrides)
+    errors = []
+
+    def cb(ctx, kind, a, b, rec):
+        try:
+            vals = get_record(kind, a, b)
+            for i in range(9):
+                rec[i] = int(vals[i])
+            return 0
+        except Exception as e:  # pragma: no cover - surfaced below
+            errors.append(e)
+            return 1
+
+    fn = N.MEASURE_FN(cb)
+    h = ctypes.c_void_p()
+    code = N.lib.analyser_detect_offline(ctypes.byref(p), width, height, nframes, fn, None, ctypes.byref(h))
+    if errors:
+        raise errors[0]
+    _check(code, "analyser_detect_offline")
+    try:
+        r = N.Results()
+        _check(N.lib.analyser_results(h, ctypes.byref(r)), "analyser_results")
+        return results_to_dict(r)
+    finally:
+        N.lib.analyser_destroy(h)
+
+
+class Server:
+    """Continuous batching of many clips on one GPU under a device-memory budget."""
+
+    def __init__(self, budget_bytes: int, params: N.Params | None = None, **overrides):
+        self.params = params if params is not None else default_params(**overrides)
+        self._h = ctypes.c_void_p()
+        _check(N.lib.server_create(ctypes.byref(self.params), int(budget_bytes), ctypes.byref(self._h)),
+               "server_create")
+        self._frames = {}
+
+    def submit(self, frames: np.ndarray, fps: float = 25.0) -> int:
+        f = np.ascontiguousarray(frames, dtype=np.uint8)
+        t = N.c_ll()
+        _check(N.lib.server_submit(self._h, f.shape[2], f.shape[1], float(fps), f.ctypes.data, f.shape[2],
+                                   f.shape[0], ctypes.byref(t)), "server_submit")
+        self._frames[t.value] = f      # the server reads it until the request is done
+        return t.value
+
+    def step(self) -> int:
+        active = ctypes.c_int()
+        _check(N.lib.server_step(self._h, ctypes.byref(active)), "server_step")
+        return active.value
+
+    def drain(self):
+        _check(N.lib.server_drain(self._h), "server_drain")
+
+    def poll(self, ticket: int):
+        r = N.Results()
+        code = _check(N.lib.server_poll(self._h, ticket, ctypes.byref(r)), "server_poll")
+        if code == N.PENDING:
+            return None
+        return results_to_dict(r)
+
+    def latency(self, ticket: int) -> float:
+        s = ctypes.c_double()
+        _check(N.lib.server_latency(self._h, ticket, ctypes.byref(s)), "server_latency")
+        return s.value
+
+    def release(self, ticket: int):
+        _check(N.lib.server_release(self._h, ticket), "server_release")
+        self._frames.pop(ticket, None)
+
+    def close(self):
+        if self._h:
+            N.lib.server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+        self._frames.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

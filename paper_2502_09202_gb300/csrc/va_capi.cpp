@@ -1,0 +1,455 @@
+// extern "C" entry points of include/analyser.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <new>
+#include <string>
+
+#include "../../include/analyser.h"
+#include "va_detect.h"
+#include "va_engine.h"
+
+struct analyser {
+  std::unique_ptr<va::Engine> eng;
+  va::Clip clip;
+  va::ResultsBuf res;
+  int status = ANALYSER_OK;
+  std::string msg;
+  bool offline = false;
+};
+
+struct server {
+  analyser_params p{};
+  unsigned long long budget = 0;
+  unsigned long long used = 0;
+  std::unique_ptr<va::Engine> eng;
+  struct Req {
+    std::unique_ptr<va::Clip> clip;
+    const uint8_t* frames = nullptr;
+    long long pitch = 0;
+    int nframes = 0, uploaded = 0;
+    bool admitted = false, done = false;
+    double t_submit = 0, t_done = 0;
+    va::ResultsBuf res;
+    size_t bytes = 0;
+  };
+  std::map<long long, Req> reqs;
+  std::deque<long long> queue;
+  long long next_ticket = 1;
+  int status = ANALYSER_OK;
+  std::string msg;
+};
+
+namespace {
+
+int fail(analyser* a, int code, const std::string& why) {
+  a->status = code;
+  a->msg = why;
+  return code;
+}
+
+int fail_srv(server* s, int code, const std::string& why) {
+  s->status = code;
+  s->msg = why;
+  return code;
+}
+
+// Run waves until the clip's detector is done (finish) or no more progress is
+// possible without new frames.
+int drive(analyser* a, bool to_end) {
+  va::Engine& e = *a->eng;
+  for (;;) {
+    const int rc = e.wave();
+    if (rc < 0 || e.status) return fail(a, e.status ? e.status : rc, e.message);
+    if (a->clip.done()) return ANALYSER_OK;
+    if (rc == 0) {
+      if (to_end) return fail(a, ANALYSER_ERR_STATE, "analysis stalled before the end of the clip");
+      return ANALYSER_OK;
+    }
+    if (!to_end && e.free_slots(&a->clip) > 0 && a->clip.pending.empty()) return ANALYSER_OK;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int analyser_default_params(analyser_params* p) {
+  if (!p) return ANALYSER_ERR_INVALID_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->block = 16;
+  p->levels = 3;
+  p->radius_coarse = 16;
+  p->radius_refine = 2;
+  p->mv_cost = 4;
+  p->kmax = 8;
+  p->jback = 2;
+  p->fast_window = 8;
+  p->fast_lambda = 2.0;
+  p->fast_rise = 1.3;
+  p->fast_tau = 0.5;
+  p->deep_rho = 2.0;
+  p->deep_tau = 0.5;
+  p->samp_max_frames = 20;
+  p->static_amm_px = 0.5;
+  p->comb_ratio = 0.3;
+  p->unequal_ratio = 1.12;
+  p->pulldown_match = 0.8;
+  p->kf_theta = 8.0;
+  p->device = 0;
+  p->window_frames = 0;
+  p->mem_budget_bytes = 0;
+  p->want_motion = 0;
+  p->tile_x = 0;
+  p->tile_y = 0;
+  return ANALYSER_OK;
+}
+
+int analyser_create(int width, int height, double fps, const analyser_params* p, analyser** out) {
+  if (!p || !out) return ANALYSER_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::string why;
+  int rc = va::validate_params(*p, why);
+  if (!rc) rc = va::validate_size(width, height, *p, why);
+  if (rc) return rc;
+  if (!(fps > 0)) return ANALYSER_ERR_INVALID_ARG;
+  analyser* a = new (std::nothrow) analyser();
+  if (!a) return ANALYSER_ERR_OOM;
+  a->eng.reset(new (std::nothrow) va::Engine(*p));
+  if (!a->eng) { delete a; return ANALYSER_ERR_OOM; }
+  rc = a->eng->init(why);
+  if (rc) { delete a; return rc; }
+  a->clip.geo.W = width;
+  a->clip.geo.H = height;
+  a->clip.fps = fps;
+  rc = a->eng->add_clip(&a->clip, why);
+  if (rc) {
+    a->eng->clips.clear();
+    delete a;
+    return rc;
+  }
+  *out = a;
+  return ANALYSER_OK;
+}
+
+int analyser_push_frames(analyser* a, const uint8_t* luma, long long pitch_bytes, int nframes) {
+  if (!a) return ANALYSER_ERR_INVALID_ARG;
+  if (a->status) return a->status;
+  if (a->offline) return ANALYSER_ERR_STATE;
+  if (a->clip.finished) return ANALYSER_ERR_STATE;
+  if (nframes < 0 || (nframes > 0 && !luma) || pitch_bytes < a->clip.geo.W) return ANALYSER_ERR_INVALID_ARG;
+  if (a->clip.external_l0) return fail(a, ANALYSER_ERR_STATE, "host and device pushes cannot be mixed");
+  va::Engine& e = *a->eng;
+  int done = 0;
+  while (done < nframes) {
+    const int k = e.upload_host(&a->clip, luma + (size_t)done * a->clip.geo.H * pitch_bytes, pitch_bytes,
+                                nframes - done);
+    if (k < 0 || e.status) return fail(a, e.status ? e.status : ANALYSER_ERR_CUDA, e.message);
+    done += k;
+    if (done < nframes) {
+      const int before = e.free_slots(&a->clip);
+      const int rc = drive(a, false);
+      if (rc) return rc;
+      if (e.free_slots(&a->clip) == 0 && before == 0) {
+        const int rc2 = e.wave();
+        if (rc2 < 0) return fail(a, e.status, e.message);
+        if (e.free_slots(&a->clip) == 0) return fail(a, ANALYSER_ERR_STATE, "frame window cannot advance");
+      }
+    }
+  }
+  // the caller may reuse its buffer once this returns
+  if (cudaStreamSynchronize(e.stream) != cudaSuccess) return fail(a, ANALYSER_ERR_CUDA, "cudaStreamSynchronize");
+  return ANALYSER_OK;
+}
+
+int analyser_push_frames_device(analyser* a, const uint8_t* luma, long long pitch_bytes, long long frame_stride_bytes,
+                                int nframes) {
+  if (!a) return ANALYSER_ERR_INVALID_ARG;
+  if (a->status) return a->status;
+  if (a->offline || a->clip.finished) return ANALYSER_ERR_STATE;
+  if (nframes < 0 || (nframes > 0 && !luma) || pitch_bytes < a->clip.geo.W || pitch_bytes % 16 ||
+      frame_stride_bytes % 16 || ((uintptr_t)luma % 16) || frame_stride_bytes < pitch_bytes * a->clip.geo.H)
+    return ANALYSER_ERR_INVALID_ARG;
+  if (a->clip.pushed > 0 && !a->clip.external_l0)
+    return fail(a, ANALYSER_ERR_STATE, "host and device pushes cannot be mixed");
+  va::Engine& e = *a->eng;
+  int done = 0;
+  while (done < nframes) {
+    const int k = e.attach_device(&a->clip, luma + (size_t)done * frame_stride_bytes, pitch_bytes, frame_stride_bytes,
+                                  nframes - done);
+    done += k;
+    if (done < nframes) {
+      const int rc = drive(a, false);
+      if (rc) return rc;
+      if (e.free_slots(&a->clip) == 0) {
+        const int rc2 = e.wave();
+        if (rc2 < 0) return fail(a, e.status, e.message);
+        if (e.free_slots(&a->clip) == 0) return fail(a, ANALYSER_ERR_STATE, "frame window cannot advance");
+      }
+    }
+  }
+  return ANALYSER_OK;
+}
+
+int analyser_finish(analyser* a) {
+  if (!a) return ANALYSER_ERR_INVALID_ARG;
+  if (a->status) return a->status;
+  if (a->offline) return ANALYSER_OK;
+  a->clip.finished = true;
+  const int rc = drive(a, true);
+  if (rc) return rc;
+  if (cudaStreamSynchronize(a->eng->stream) != cudaSuccess) return fail(a, ANALYSER_ERR_CUDA, "cudaStreamSynchronize");
+  return ANALYSER_OK;
+}
+
+int analyser_results(analyser* a, analyser_results_t* out) {
+  if (!a || !out) return ANALYSER_ERR_INVALID_ARG;
+  if (a->status) return a->status;
+  if (!a->clip.done()) return ANALYSER_ERR_STATE;
+  va::build_results(a->clip, a->res);
+  *out = a->res.r;
+  return ANALYSER_OK;
+}
+
+int analyser_last_error(const analyser* a, const char** message) {
+  if (!a) return ANALYSER_ERR_INVALID_ARG;
+  if (message) *message = a->msg.c_str();
+  return a->status;
+}
+
+int analyser_stats(const analyser* a, long long* pairs, long long* waves, long long* launches) {
+  if (!a) return ANALYSER_ERR_INVALID_ARG;
+  if (pairs) *pairs = a->eng ? a->eng->n_pairs : 0;
+  if (waves) *waves = a->eng ? a->eng->n_waves : 0;
+  if (launches) *launches = a->eng ? a->eng->n_launches : 0;
+  return ANALYSER_OK;
+}
+
+void analyser_destroy(analyser* a) {
+  if (!a) return;
+  if (a->eng) {
+    a->eng->remove_clip(&a->clip);
+    if (a->eng->stream) cudaStreamSynchronize(a->eng->stream);
+  }
+  delete a;
+}
+
+int analyser_measure_pairs(const analyser_params* p, int width, int height, const uint8_t* frames,
+                           long long pitch_bytes, long long frame_stride_bytes, int nframes, const int* kinds,
+                           const int* ia, const int* ib, int npairs, int64_t* records, int16_t* motion,
+                           void* stream) {
+  if (!p) return ANALYSER_ERR_INVALID_ARG;
+  va::Engine e(*p);
+  std::string why;
+  int rc = e.init(why);
+  if (rc) return rc;
+  e.autotune = false;
+  return e.measure_pairs(width, height, frames, pitch_bytes, frame_stride_bytes, nframes, kinds, ia, ib, npairs,
+                         records, motion, (cudaStream_t)stream, why);
+}
+
+int analyser_detect_offline(const analyser_params* p, int width, int height, int nframes, analyser_measure_fn get,
+                            void* ctx, analyser** out) {
+  if (!p || !get || !out || nframes < 0) return ANALYSER_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::string why;
+  int rc = va::validate_params(*p, why);
+  if (!rc) rc = va::validate_size(width, height, *p, why);
+  if (rc) return rc;
+  analyser* a = new (std::nothrow) analyser();
+  if (!a) return ANALYSER_ERR_OOM;
+  a->offline = true;
+  va::Clip& c = a->clip;
+  c.p = *p;
+  c.geo.init(width, height, p->levels);
+  c.pushed = nframes;
+  c.finished = true;
+  c.det.reset(*p, (int64_t)(width / c.geo.B0) * (height / c.geo.B0));
+  auto fetch = [&](uint64_t key) -> int {
+    int64_t rec[9];
+    if (get(ctx, va::key_kind(key), va::key_a(key), va::key_b(key), rec)) return ANALYSER_ERR_INVALID_ARG;
+    va::Measure m;
+    for (int k = 0; k < 7; k++) m.s[k] = rec[k];
+    m.n = rec[7];
+    m.nb = rec[8];
+    m.used = va::key_kind(key) == va::kFrame && va::key_b(key) == va::key_a(key) + 1;
+    va::finalise_measure(m);
+    c.store.map[key] = m;
+    return ANALYSER_OK;
+  };
+  for (int t = 0; t + 1 < nframes; t++) {
+    if (fetch(va::pair_key(va::kFrame, t, t + 1))) { delete a; return ANALYSER_ERR_INVALID_ARG; }
+  }
+  for (int guard = 0; guard < 10000000 && !c.det.done(); guard++) {
+    std::vector<uint64_t> need;
+    c.det.run(c.store, nframes, true, need);
+    std::sort(need.begin(), need.end());
+    need.erase(std::unique(need.begin(), need.end()), need.end());
+    for (uint64_t k : need)
+      if (!c.store.map.count(k) && fetch(k)) { delete a; return ANALYSER_ERR_INVALID_ARG; }
+    if (need.empty() && !c.det.done()) { delete a; return ANALYSER_ERR_STATE; }
+  }
+  *out = a;
+  return ANALYSER_OK;
+}
+
+// ---------------------------------------------------------------------------
+// serving
+// ---------------------------------------------------------------------------
+
+int server_create(const analyser_params* p, unsigned long long budget_bytes, server** out) {
+  if (!p || !out) return ANALYSER_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::string why;
+  int rc = va::validate_params(*p, why);
+  if (rc) return rc;
+  server* s = new (std::nothrow) server();
+  if (!s) return ANALYSER_ERR_OOM;
+  s->p = *p;
+  s->budget = budget_bytes;
+  s->eng.reset(new (std::nothrow) va::Engine(*p));
+  if (!s->eng) { delete s; return ANALYSER_ERR_OOM; }
+  rc = s->eng->init(why);
+  if (rc) { delete s; return rc; }
+  *out = s;
+  return ANALYSER_OK;
+}
+
+int server_submit(server* s, int width, int height, double fps, const uint8_t* frames, long long pitch_bytes,
+                  int nframes, long long* ticket) {
+  if (!s || !ticket || nframes < 0 || (nframes > 0 && !frames) || pitch_bytes < width || !(fps > 0))
+    return ANALYSER_ERR_INVALID_ARG;
+  if (s->status) return s->status;
+  std::string why;
+  int rc = va::validate_size(width, height, s->p, why);
+  if (rc) return rc;
+  const long long t = s->next_ticket++;
+  server::Req& r = s->reqs[t];
+  r.clip.reset(new (std::nothrow) va::Clip());
+  if (!r.clip) { s->reqs.erase(t); return ANALYSER_ERR_OOM; }
+  r.clip->id = t;
+  r.clip->geo.W = width;
+  r.clip->geo.H = height;
+  r.clip->fps = fps;
+  r.frames = frames;
+  r.pitch = pitch_bytes;
+  r.nframes = nframes;
+  r.t_submit = va::now_seconds();
+  r.clip->t_submit = r.t_submit;
+  // window size is fixed at admission; estimate its bytes now for the budget
+  va::Geometry g;
+  g.init(width, height, s->p.levels);
+  const int cap = s->p.window_frames > 0 ? s->p.window_frames : std::max(96, 2 * s->p.kmax + 8);
+  r.bytes = va::Engine::ring_bytes(g, cap);
+  if (s->budget && r.bytes > s->budget) {
+    s->reqs.erase(t);
+    return ANALYSER_ERR_OOM;
+  }
+  s->queue.push_back(t);
+  *ticket = t;
+  return ANALYSER_OK;
+}
+
+int server_step(server* s, int* active) {
+  if (!s) return ANALYSER_ERR_INVALID_ARG;
+  if (s->status) return s->status;
+  va::Engine& e = *s->eng;
+  // admission: first come, first served, while the budget allows
+  while (!s->queue.empty()) {
+    server::Req& r = s->reqs[s->queue.front()];
+    if (s->budget && s->used + r.bytes > s->budget) break;
+    std::string why;
+    const int rc = e.add_clip(r.clip.get(), why);
+    if (rc == ANALYSER_ERR_OOM && !e.clips.empty()) break;   // retry when memory frees up
+    if (rc) return fail_srv(s, rc, why);
+    r.admitted = true;
+    s->used += r.bytes;
+    s->queue.pop_front();
+  }
+  // top up every admitted clip's window
+  for (auto& kv : s->reqs) {
+    server::Req& r = kv.second;
+    if (!r.admitted || r.done) continue;
+    if (r.uploaded < r.nframes) {
+      const int k = e.upload_host(r.clip.get(), r.frames + (size_t)r.uploaded * r.clip->geo.H * r.pitch, r.pitch,
+                                  r.nframes - r.uploaded);
+      if (k < 0) return fail_srv(s, e.status, e.message);
+      r.uploaded += k;
+    }
+    if (r.uploaded == r.nframes) r.clip->finished = true;
+  }
+  const int rc = e.wave();
+  if (rc < 0 || e.status) return fail_srv(s, e.status ? e.status : rc, e.message);
+  // retire finished clips
+  int n_active = (int)s->queue.size();
+  for (auto& kv : s->reqs) {
+    server::Req& r = kv.second;
+    if (!r.admitted || r.done) continue;
+    if (r.clip->done()) {
+      va::build_results(*r.clip, r.res);
+      r.t_done = r.clip->t_done > 0 ? r.clip->t_done : va::now_seconds();
+      e.remove_clip(r.clip.get());
+      s->used -= r.bytes;
+      r.done = true;
+      r.clip->store.map.clear();
+    } else {
+      n_active++;
+      if (rc == 0 && r.uploaded == r.nframes && r.clip->pending.empty())
+        return fail_srv(s, ANALYSER_ERR_STATE, "a served clip stalled");
+    }
+  }
+  if (active) *active = n_active;
+  return ANALYSER_OK;
+}
+
+int server_drain(server* s) {
+  if (!s) return ANALYSER_ERR_INVALID_ARG;
+  for (;;) {
+    int active = 0;
+    const int rc = server_step(s, &active);
+    if (rc) return rc;
+    if (active == 0) return ANALYSER_OK;
+  }
+}
+
+int server_poll(server* s, long long ticket, analyser_results_t* out) {
+  if (!s || !out) return ANALYSER_ERR_INVALID_ARG;
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return ANALYSER_ERR_INVALID_ARG;
+  if (s->status) return s->status;
+  if (!it->second.done) return ANALYSER_PENDING;
+  *out = it->second.res.r;
+  return ANALYSER_OK;
+}
+
+int server_latency(const server* s, long long ticket, double* seconds) {
+  if (!s || !seconds) return ANALYSER_ERR_INVALID_ARG;
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return ANALYSER_ERR_INVALID_ARG;
+  if (!it->second.done) return ANALYSER_PENDING;
+  *seconds = it->second.t_done - it->second.t_submit;
+  return ANALYSER_OK;
+}
+
+int server_release(server* s, long long ticket) {
+  if (!s) return ANALYSER_ERR_INVALID_ARG;
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end() || !it->second.done) return ANALYSER_ERR_STATE;
+  s->reqs.erase(it);
+  return ANALYSER_OK;
+}
+
+void server_destroy(server* s) {
+  if (!s) return;
+  if (s->eng) {
+    for (auto& kv : s->reqs)
+      if (kv.second.admitted && !kv.second.done) s->eng->remove_clip(kv.second.clip.get());
+  }
+  delete s;
+}
+
+}  // extern "C"

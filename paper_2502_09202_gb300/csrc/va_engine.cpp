@@ -1,0 +1,676 @@
+// Runtime of the analyser (see va_engine.h).
+#include "va_engine.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <map>
+
+namespace va {
+
+#define VA_CUDA_TRY(call, why)                                                        \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      why = std::string(#call) + ": " + cudaGetErrorString(e_);                       \
+      return ANALYSER_ERR_CUDA;                                                       \
+    }                                                                                 \
+  } while (0)
+
+double now_seconds() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+static inline size_t round_up_sz(size_t v, size_t m) { return (v + m - 1) / m * m; }
+
+// floor(sqrt(n)), digit-by-digit (binary restoring) method
+static uint64_t isqrt_digits(uint64_t n) {
+  uint64_t res = 0, bit = 1ull << 62;
+  while (bit > n) bit >>= 2;
+  while (bit) {
+    if (n >= res + bit) {
+      n -= res + bit;
+      res = (res >> 1) + bit;
+    } else {
+      res >>= 1;
+    }
+    bit >>= 2;
+  }
+  return res;
+}
+
+int validate_params(const analyser_params& p, std::string& why) {
+  if (p.levels < 2 || p.levels > 3) { why = "levels must be 2 or 3"; return ANALYSER_ERR_INVALID_ARG; }
+  if (p.block != (kCoarseSide << (p.levels - 1))) {
+    why = "block must equal 4 << (levels-1)";
+    return ANALYSER_ERR_INVALID_ARG;
+  }
+  if (p.radius_coarse != 8 && p.radius_coarse != 16 && p.radius_coarse != 24) {
+    why = "radius_coarse must be 8, 16 or 24";
+    return ANALYSER_ERR_INVALID_ARG;
+  }
+  if (p.radius_refine < 0 || p.radius_refine > 4) { why = "radius_refine must be 0..4"; return ANALYSER_ERR_INVALID_ARG; }
+  if (p.mv_cost < 0 || p.mv_cost > 64) { why = "mv_cost must be 0..64"; return ANALYSER_ERR_INVALID_ARG; }
+  if (p.kmax < 1 || p.kmax > 16) { why = "kmax must be 1..16"; return ANALYSER_ERR_INVALID_ARG; }
+  if (p.jback < 1 || p.jback > 64) { why = "jback must be 1..64"; return ANALYSER_ERR_INVALID_ARG; }
+  if (p.fast_window < 1 || p.fast_window > 1024) { why = "fast_window must be 1..1024"; return ANALYSER_ERR_INVALID_ARG; }
+  if (p.samp_max_frames < 0 || p.samp_max_frames > 100000) { why = "samp_max_frames out of range"; return ANALYSER_ERR_INVALID_ARG; }
+  if (!(p.fast_lambda >= 0) || !(p.fast_rise >= 0) || !(p.fast_tau >= 0) || !(p.deep_rho >= 0) || !(p.deep_tau >= 0) ||
+      !(p.static_amm_px >= 0) || !(p.comb_ratio >= 0) || !(p.unequal_ratio >= 0) || !(p.pulldown_match >= 0) ||
+      !(p.kf_theta >= 0)) {
+    why = "thresholds must be non-negative numbers";
+    return ANALYSER_ERR_INVALID_ARG;
+  }
+  if ((p.tile_x || p.tile_y) && !pair_tile_supported(p.radius_coarse, p.tile_x, p.tile_y)) {
+    why = "tile_x x tile_y is not a compiled tile shape";
+    return ANALYSER_ERR_INVALID_ARG;
+  }
+  if (p.window_frames != 0 && p.window_frames < 2 * p.kmax + 6) {
+    why = "window_frames must be 0 (auto) or >= 2*kmax+6";
+    return ANALYSER_ERR_INVALID_ARG;
+  }
+  return ANALYSER_OK;
+}
+
+int validate_size(int width, int height, const analyser_params& p, std::string& why) {
+  (void)p;
+  if (width < 64 || height < 64) { why = "width and height must be >= 64"; return ANALYSER_ERR_INVALID_ARG; }
+  if (height % 2) { why = "height must be even (two equal fields)"; return ANALYSER_ERR_INVALID_ARG; }
+  if ((long long)width * height > 11800000LL) {
+    why = "width*height must be <= 11,800,000 (exact 64-bit correlation sums)";
+    return ANALYSER_ERR_INVALID_ARG;
+  }
+  return ANALYSER_OK;
+}
+
+void Geometry::init(int width, int height, int levels, bool own_l0) {
+  W = width; H = height; L = levels; B0 = kCoarseSide << (levels - 1);
+  fw[0] = W; fh[0] = H; fp[0] = round_up(W, 64);
+  gw[0] = W; gh[0] = H / 2; gp[0] = 2 * fp[0];
+  for (int l = 1; l < L; l++) {
+    fw[l] = fw[l - 1] / 2; fh[l] = fh[l - 1] / 2; fp[l] = round_up(std::max(fw[l], 4), 16);
+    gw[l] = gw[l - 1] / 2; gh[l] = gh[l - 1] / 2; gp[l] = round_up(std::max(gw[l], 4), 16);
+  }
+  size_t off = 0;
+  l0_bytes = own_l0 ? round_up_sz((size_t)fh[0] * fp[0] + 64, 256) : 0;
+  off = l0_bytes;
+  for (int l = 1; l < L; l++) { off_f[l] = off; off += round_up_sz((size_t)fh[l] * fp[l] + 16, 256); }
+  for (int l = 1; l < L; l++) { off_u[l] = off; off += round_up_sz((size_t)gh[l] * gp[l] + 16, 256); }
+  for (int l = 1; l < L; l++) { off_l[l] = off; off += round_up_sz((size_t)gh[l] * gp[l] + 16, 256); }
+  slot_bytes = off;
+}
+
+Engine::Engine(const analyser_params& params) : p(params) {}
+
+Engine::~Engine() {
+  for (Clip* c : clips) if (c->d_ring) cudaFree(c->d_ring);
+  if (d_qtab) cudaFree(d_qtab);
+  if (d_status) cudaFree(d_status);
+  if (h_status) cudaFreeHost(h_status);
+  if (d_pjobs) cudaFree(d_pjobs);
+  if (h_pjobs) cudaFreeHost(h_pjobs);
+  if (d_djobs) cudaFree(d_djobs);
+  if (h_djobs) cudaFreeHost(h_djobs);
+  if (d_rec) cudaFree(d_rec);
+  if (h_rec) cudaFreeHost(h_rec);
+  if (d_vec) cudaFree(d_vec);
+  if (stream) cudaStreamDestroy(stream);
+}
+
+int Engine::init(std::string& why) {
+  int rc = validate_params(p, why);
+  if (rc) return rc;
+  VA_CUDA_TRY(cudaSetDevice(p.device), why);
+  VA_CUDA_TRY(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking), why);
+  VA_CUDA_TRY(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, p.device), why);
+  // Q(k) = floor(sqrt(k) * 2^16) for every k = vx^2 + vy^2 the search can produce
+  int vmax = p.radius_coarse;
+  for (int l = p.levels - 2; l >= 0; l--) vmax = 2 * vmax + p.radius_refine;
+  qmax = 2 * vmax * vmax;
+  std::vector<uint32_t> q(qmax + 1);
+  for (int k = 0; k <= qmax; k++) q[k] = (uint32_t)isqrt_digits((uint64_t)k << 32);
+  VA_CUDA_TRY(cudaMalloc(&d_qtab, sizeof(uint32_t) * (qmax + 1)), why);
+  VA_CUDA_TRY(cudaMemcpy(d_qtab, q.data(), sizeof(uint32_t) * (qmax + 1), cudaMemcpyHostToDevice), why);
+  VA_CUDA_TRY(cudaMalloc(&d_status, sizeof(int)), why);
+  VA_CUDA_TRY(cudaMemset(d_status, 0, sizeof(int)), why);
+  VA_CUDA_TRY(cudaMallocHost(&h_status, sizeof(int)), why);
+  return ANALYSER_OK;
+}
+
+size_t Engine::ring_bytes(const Geometry& g, int cap) { return (size_t)cap * g.slot_bytes; }
+
+int Engine::add_clip(Clip* c, std::string& why, bool enlist) {
+  c->p = p;
+  c->want_vec_ = c->want_vec_ || (!c->stateless_ && p.want_motion);
+  c->geo.init(c->geo.W, c->geo.H, p.levels, !c->external_l0);
+  if (c->cap <= 0) c->cap = p.window_frames > 0 ? p.window_frames : std::max(96, 2 * p.kmax + 8);
+  c->l0.assign(c->cap, nullptr);
+  c->l0_pitch.assign(c->cap, 0);
+  const size_t bytes = ring_bytes(c->geo, c->cap);
+  if (p.mem_budget_bytes && bytes > p.mem_budget_bytes) {
+    why = "rolling window exceeds mem_budget_bytes";
+    return ANALYSER_ERR_OOM;
+  }
+  cudaError_t e = cudaMalloc(&c->d_ring, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    why = std::string("cudaMalloc(window): ") + cudaGetErrorString(e);
+    return ANALYSER_ERR_OOM;
+  }
+  for (int s = 0; s < c->cap; s++) {
+    c->l0[s] = c->d_ring + (size_t)s * c->geo.slot_bytes;
+    c->l0_pitch[s] = c->geo.fp[0];
+  }
+  const int nbx = c->geo.W / c->geo.B0, nby = c->geo.H / c->geo.B0;
+  c->det.reset(p, (int64_t)nbx * nby);
+  if (p.tile_x > 0) {
+    c->tbx = p.tile_x;
+    c->tby = p.tile_y;
+  } else if (!c->stateless_) {
+    choose_tile(c->geo.W, c->geo.H, &c->tbx, &c->tby);
+  }
+  if (enlist) clips.push_back(c);
+  return ANALYSER_OK;
+}
+
+void Engine::remove_clip(Clip* c) {
+  clips.erase(std::remove(clips.begin(), clips.end(), c), clips.end());
+  if (c->d_ring) {
+    cudaFree(c->d_ring);
+    c->d_ring = nullptr;
+  }
+}
+
+int Engine::upload_host(Clip* c, const uint8_t* frames, long long pitch, int nframes) {
+  const int k = std::min(nframes, free_slots(c));
+  const Geometry& g = c->geo;
+  for (int i = 0; i < k; i++) {
+    const int f = c->pushed + i;
+    const int s = c->slot_of(f);
+    uint8_t* dst = c->d_ring + (size_t)s * g.slot_bytes;
+    cudaError_t e = cudaMemcpy2DAsync(dst, g.fp[0], frames + (size_t)i * g.H * pitch, pitch, g.W, g.H,
+                                      cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) {
+      status = ANALYSER_ERR_CUDA;
+      message = std::string("cudaMemcpy2DAsync(frame): ") + cudaGetErrorString(e);
+      return -1;
+    }
+    c->l0[s] = dst;
+    c->l0_pitch[s] = g.fp[0];
+  }
+  c->pushed += k;
+  return k;
+}
+
+int Engine::attach_device(Clip* c, const uint8_t* frames, long long pitch, long long stride, int nframes) {
+  const int k = std::min(nframes, free_slots(c));
+  for (int i = 0; i < k; i++) {
+    const int f = c->pushed + i;
+    const int s = c->slot_of(f);
+    c->l0[s] = frames + (size_t)i * stride;
+    c->l0_pitch[s] = (int)pitch;
+  }
+  c->external_l0 = true;
+  c->pushed += k;
+  return k;
+}
+
+void Engine::choose_tile(int width, int height, int* tbx, int* tby) {
+  for (size_t i = 0; i < tune_keys_.size(); i++)
+    if (tune_keys_[i] == std::make_pair(width, height)) {
+      *tbx = tune_vals_[i].first;
+      *tby = tune_vals_[i].second;
+      return;
+    }
+  int bx = 8, by = 4;
+  if (autotune && stream) {
+    // time every compiled tile shape on a batch of synthetic pairs of this size;
+    // the tile changes the schedule only, never the result
+    const int B0 = kCoarseSide << (p.levels - 1);
+    const int nblk = std::max(1, (width / B0) * (height / B0));
+    const int reps = std::max(4, std::min(32, 400000 / nblk + 1));
+    const long long pitch = round_up(width, 64);
+    const long long stride = pitch * height;
+    const int nfr = reps + 1;
+    uint8_t* d = nullptr;
+    if (cudaMalloc(&d, (size_t)stride * nfr) == cudaSuccess) {
+      std::vector<uint8_t> h((size_t)stride * nfr);
+      uint32_t st = 12345;
+      for (size_t i = 0; i < h.size(); i++) { st = st * 1664525u + 1013904223u; h[i] = (uint8_t)(st >> 24); }
+      cudaMemcpy(d, h.data(), h.size(), cudaMemcpyHostToDevice);
+      Clip c;
+      c.geo.W = width;
+      c.geo.H = height;
+      c.cap = nfr;
+      c.stateless_ = true;
+      c.external_l0 = true;
+      std::string why;
+      if (add_clip(&c, why, false) == ANALYSER_OK) {
+        attach_device(&c, d, pitch, stride, nfr);
+        const int cand[5][2] = {{8, 4}, {4, 4}, {8, 2}, {16, 2}, {4, 8}};
+        double best_s = 1e30;
+        for (auto& cd : cand) {
+          if (!pair_tile_supported(p.radius_coarse, cd[0], cd[1])) continue;
+          c.tbx = cd[0];
+          c.tby = cd[1];
+          double tsum = 0.0;
+          bool ok = true;
+          for (int it = 0; it < 3 && ok; it++) {
+            c.store.map.clear();
+            c.pyr_done = it == 0 ? 0 : c.pushed;
+            for (int i = 0; i < reps; i++) c.pending.push_back(pair_key(kFrame, i, i + 1));
+            const double t0 = now_seconds();
+            if (run_alone(&c) < 0) ok = false;
+            const double t1 = now_seconds();
+            if (it > 0) tsum += t1 - t0;
+          }
+          if (ok && tsum < best_s) { best_s = tsum; bx = cd[0]; by = cd[1]; }
+        }
+        cudaFree(c.d_ring);
+        c.d_ring = nullptr;
+      }
+      cudaFree(d);
+    }
+    cudaGetLastError();
+    status = ANALYSER_OK;
+    message.clear();
+  }
+  tune_keys_.push_back({width, height});
+  tune_vals_.push_back({bx, by});
+  *tbx = bx;
+  *tby = by;
+}
+
+int Engine::run_alone(Clip* c) {
+  std::vector<Clip*> saved;
+  saved.swap(clips);
+  clips.push_back(c);
+  const int rc = wave();
+  clips.swap(saved);
+  return status ? status : rc;
+}
+
+int Engine::ensure_capacity(int npairs, int ndown) {
+  std::string why;
+  if (npairs > cap_pairs) {
+    int nc = std::max(npairs, std::max(256, cap_pairs * 2));
+    if (d_pjobs) cudaFree(d_pjobs);
+    if (h_pjobs) cudaFreeHost(h_pjobs);
+    if (d_rec) cudaFree(d_rec);
+    if (h_rec) cudaFreeHost(h_rec);
+    d_pjobs = nullptr; h_pjobs = nullptr; d_rec = nullptr; h_rec = nullptr;
+    VA_CUDA_TRY(cudaMalloc(&d_pjobs, sizeof(PairJob) * nc), message);
+    VA_CUDA_TRY(cudaMallocHost(&h_pjobs, sizeof(PairJob) * nc), message);
+    VA_CUDA_TRY(cudaMalloc(&d_rec, sizeof(unsigned long long) * kRecWords * nc), message);
+    VA_CUDA_TRY(cudaMallocHost(&h_rec, sizeof(unsigned long long) * kRecWords * nc), message);
+    cap_pairs = nc;
+  }
+  if (ndown > cap_down) {
+    int nc = std::max(ndown, std::max(256, cap_down * 2));
+    if (d_djobs) cudaFree(d_djobs);
+    if (h_djobs) cudaFreeHost(h_djobs);
+    d_djobs = nullptr; h_djobs = nullptr;
+    VA_CUDA_TRY(cudaMalloc(&d_djobs, sizeof(DownJob) * nc), message);
+    VA_CUDA_TRY(cudaMallocHost(&h_djobs, sizeof(DownJob) * nc), message);
+    cap_down = nc;
+  }
+  return ANALYSER_OK;
+}
+
+int Engine::setup_pair_job(const Clip& c, uint64_t key, PairJob& pj, int item_begin, unsigned long long* rec,
+                           short2* vec) {
+  const Geometry& g = c.geo;
+  const int kind = key_kind(key), a = key_a(key), b = key_b(key);
+  const int sa = c.slot_of(a), sb = c.slot_of(b);
+  const uint8_t* ra = c.d_ring + (size_t)sa * g.slot_bytes;
+  const uint8_t* rb = c.d_ring + (size_t)sb * g.slot_bytes;
+  const uint8_t* la = c.l0[sa];
+  const uint8_t* lb = c.l0[sb];
+  const int pa = c.l0_pitch[sa], pb = c.l0_pitch[sb];
+  if (kind == kFrame) {
+    pj.I[0] = {la, pa, g.W, g.H};
+    pj.J[0] = {lb, pb, g.W, g.H};
+    for (int l = 1; l < g.L; l++) {
+      pj.I[l] = {ra + g.off_f[l], g.fp[l], g.fw[l], g.fh[l]};
+      pj.J[l] = {rb + g.off_f[l], g.fp[l], g.fw[l], g.fh[l]};
+    }
+    pj.nbx = g.W / g.B0;
+    pj.nby = g.H / g.B0;
+  } else {
+    const bool ul = kind == kUpperLower;
+    // level-0 fields are row-strided views of the frames
+    pj.I[0] = {ul ? la : la + pa, 2 * pa, g.W, g.H / 2};
+    pj.J[0] = {ul ? lb + pb : lb, 2 * pb, g.W, g.H / 2};
+    for (int l = 1; l < g.L; l++) {
+      pj.I[l] = {ra + (ul ? g.off_u[l] : g.off_l[l]), g.gp[l], g.gw[l], g.gh[l]};
+      pj.J[l] = {rb + (ul ? g.off_l[l] : g.off_u[l]), g.gp[l], g.gw[l], g.gh[l]};
+    }
+    pj.nbx = g.W / g.B0;
+    pj.nby = (g.H / 2) / g.B0;
+  }
+  pj.tiles_x = (pj.nbx + c.tbx - 1) / c.tbx;
+  pj.tiles_y = (pj.nby + c.tby - 1) / c.tby;
+  pj.item_begin = item_begin;
+  pj.rec = rec;
+  pj.vec = vec;
+  return pj.tiles_x * pj.tiles_y;
+}
+
+int Engine::wave() {
+  if (status) return status;
+  wp_.clear();
+  // detectors with nothing queued may be able to move on (new frames, finish)
+  for (Clip* c : clips) {
+    if (c->status || c->stateless_ || c->done() || !c->pending.empty()) continue;
+    std::vector<uint64_t> need;
+    c->det.run(c->store, c->pushed, c->finished, need);
+    std::sort(need.begin(), need.end());
+    need.erase(std::unique(need.begin(), need.end()), need.end());
+    c->pending = need;
+    if (c->done() && c->t_done < 0) c->t_done = now_seconds();
+  }
+  // ---- gather ---------------------------------------------------------------
+  std::vector<DownJob> down[kMaxLevels];
+  for (Clip* c : clips) {
+    if (c->status || c->done()) continue;
+    const Geometry& g = c->geo;
+    for (int f = c->pyr_done; f < c->pushed; f++) {
+      const int s = c->slot_of(f);
+      uint8_t* base = c->d_ring + (size_t)s * g.slot_bytes;
+      const uint8_t* l0 = c->l0[s];
+      const int p0 = c->l0_pitch[s];
+      // level 1 from level 0: frame, upper field, lower field
+      down[1].push_back({{l0, p0, g.W, g.H}, base + g.off_f[1], g.fp[1]});
+      down[1].push_back({{l0, 2 * p0, g.W, g.H / 2}, base + g.off_u[1], g.gp[1]});
+      down[1].push_back({{l0 + p0, 2 * p0, g.W, g.H / 2}, base + g.off_l[1], g.gp[1]});
+      for (int l = 2; l < g.L; l++) {
+        down[l].push_back({{base + g.off_f[l - 1], g.fp[l - 1], g.fw[l - 1], g.fh[l - 1]}, base + g.off_f[l], g.fp[l]});
+        down[l].push_back({{base + g.off_u[l - 1], g.gp[l - 1], g.gw[l - 1], g.gh[l - 1]}, base + g.off_u[l], g.gp[l]});
+        down[l].push_back({{base + g.off_l[l - 1], g.gp[l - 1], g.gw[l - 1], g.gh[l - 1]}, base + g.off_l[l], g.gp[l]});
+      }
+    }
+    c->pyr_done = c->pushed;
+    auto want = [&](uint64_t k) {
+      if (c->store.map.count(k) || c->inflight.count(k)) return;
+      c->inflight.insert(k);
+      wp_.push_back({c, k, 0, c->tbx, c->tby});
+    };
+    if (!c->stateless_) {
+      for (int t = c->aon_next; t < c->pushed - 1; t++) want(pair_key(kFrame, t, t + 1));
+      c->aon_next = std::max(c->aon_next, c->pushed - 1);
+    }
+    for (uint64_t k : c->pending) want(k);
+    c->pending.clear();
+  }
+  int ndown = 0;
+  for (int l = 1; l < kMaxLevels; l++) ndown += (int)down[l].size();
+  const int npairs = (int)wp_.size();
+  if (npairs == 0 && ndown == 0) return 0;
+  if (ensure_capacity(npairs, ndown)) { status = ANALYSER_ERR_CUDA; return status; }
+
+  // ---- pair jobs, grouped by tile shape ---------------------------------------
+  std::stable_sort(wp_.begin(), wp_.end(), [](const WavePair& x, const WavePair& y) {
+    return x.tbx != y.tbx ? x.tbx < y.tbx : x.tby < y.tby;
+  });
+  size_t vec_total = 0;
+  for (auto& w : wp_) {
+    const bool dump = w.clip->want_vec_ && key_kind(w.key) == kFrame;
+    if (dump) {
+      const Geometry& g = w.clip->geo;
+      w.vec_off = vec_total + 1;
+      vec_total += (size_t)(g.W / g.B0) * (g.H / g.B0);
+    }
+  }
+  if (vec_total > cap_vec) {
+    if (d_vec) cudaFree(d_vec);
+    d_vec = nullptr;
+    if (cudaMalloc(&d_vec, sizeof(short2) * vec_total) != cudaSuccess) {
+      status = ANALYSER_ERR_OOM; message = "cudaMalloc(motion dump)"; return status;
+    }
+    cap_vec = vec_total;
+  }
+  struct Group { int first, count, items, tbx, tby; };
+  std::vector<Group> groups;
+  int items = 0;
+  for (int i = 0; i < npairs; i++) {
+    WavePair& w = wp_[i];
+    if (groups.empty() || groups.back().tbx != w.tbx || groups.back().tby != w.tby) {
+      groups.push_back({i, 0, 0, w.tbx, w.tby});
+      items = 0;
+    }
+    short2* vp = w.vec_off ? d_vec + (w.vec_off - 1) : nullptr;
+    const int n = setup_pair_job(*w.clip, w.key, h_pjobs[i], items, d_rec + (size_t)kRecWords * i, vp);
+    items += n;
+    groups.back().count++;
+    groups.back().items = items;
+  }
+  int di = 0;
+  int dstart[kMaxLevels] = {0}, dcount[kMaxLevels] = {0}, dmaxh[kMaxLevels] = {0}, dmaxw[kMaxLevels] = {0};
+  for (int l = 1; l < kMaxLevels; l++) {
+    dstart[l] = di;
+    for (const DownJob& j : down[l]) {
+      h_djobs[di++] = j;
+      dmaxh[l] = std::max(dmaxh[l], j.src.h / 2);
+      dmaxw[l] = std::max(dmaxw[l], j.src.w / 2);
+    }
+    dcount[l] = (int)down[l].size();
+  }
+
+  // ---- launch -----------------------------------------------------------------
+  std::string& why = message;
+  auto fail = [&](cudaError_t e, const char* what) {
+    status = ANALYSER_ERR_CUDA;
+    message = std::string(what) + ": " + cudaGetErrorString(e);
+    return status;
+  };
+  cudaError_t e;
+  (void)why;
+  if (npairs) {
+    e = cudaMemcpyAsync(d_pjobs, h_pjobs, sizeof(PairJob) * npairs, cudaMemcpyHostToDevice, stream);
+    if (e) return fail(e, "cudaMemcpyAsync(pair jobs)");
+    e = cudaMemsetAsync(d_rec, 0, sizeof(unsigned long long) * kRecWords * npairs, stream);
+    if (e) return fail(e, "cudaMemsetAsync(records)");
+  }
+  if (ndown) {
+    e = cudaMemcpyAsync(d_djobs, h_djobs, sizeof(DownJob) * ndown, cudaMemcpyHostToDevice, stream);
+    if (e) return fail(e, "cudaMemcpyAsync(pyramid jobs)");
+  }
+  for (int l = 1; l < kMaxLevels; l++) {
+    if (!dcount[l]) continue;
+    e = launch_downsample(d_djobs + dstart[l], dcount[l], dmaxh[l], dmaxw[l], stream);
+    if (e) return fail(e, "downsample_kernel");
+    n_launches++;
+  }
+  for (const Group& gr : groups) {
+    PairBatch b;
+    b.jobs = d_pjobs + gr.first;
+    b.njobs = gr.count;
+    b.nitems = gr.items;
+    b.qtab = d_qtab;
+    b.qmax = qmax;
+    b.cfg = {p.levels, p.radius_coarse, p.radius_refine, p.mv_cost};
+    b.status = d_status;
+    const int nt = pair_threads(p.radius_coarse, gr.tbx, gr.tby);
+    int per_sm = 1;
+    (void)nt;
+    per_sm = pair_blocks_per_sm(p.radius_coarse, gr.tbx, gr.tby);
+    const int grid = std::max(1, std::min(gr.items, sm_count * std::max(per_sm, 1)));
+    e = launch_pairs(b, gr.tbx, gr.tby, grid, stream);
+    if (e) return fail(e, "pair_kernel");
+    n_launches++;
+  }
+  if (npairs) {
+    e = cudaMemcpyAsync(h_rec, d_rec, sizeof(unsigned long long) * kRecWords * npairs, cudaMemcpyDeviceToHost, stream);
+    if (e) return fail(e, "cudaMemcpyAsync(records)");
+    if (vec_total) {
+      h_vec.resize(vec_total);
+      e = cudaMemcpyAsync(h_vec.data(), d_vec, sizeof(short2) * vec_total, cudaMemcpyDeviceToHost, stream);
+      if (e) return fail(e, "cudaMemcpyAsync(motion)");
+    }
+  }
+  e = cudaMemcpyAsync(h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, stream);
+  if (e) return fail(e, "cudaMemcpyAsync(status)");
+  e = cudaStreamSynchronize(stream);
+  if (e) return fail(e, "cudaStreamSynchronize(wave)");
+  const int dev_status = *h_status;
+  if (dev_status) {
+    status = ANALYSER_ERR_CUDA;
+    message = "device-side check failed in pair_kernel (motion vector outside the AMM table)";
+    return status;
+  }
+  n_waves++;
+  n_pairs += npairs;
+
+  // ---- results ------------------------------------------------------------------
+  for (int i = 0; i < npairs; i++) {
+    WavePair& w = wp_[i];
+    Clip* c = w.clip;
+    Measure m;
+    for (int k = 0; k < kRecWords; k++) m.s[k] = (int64_t)h_rec[(size_t)kRecWords * i + k];
+    const Geometry& g = c->geo;
+    const int kind = key_kind(w.key);
+    const int h0 = kind == kFrame ? g.H : g.H / 2;
+    m.n = (int64_t)g.W * h0;
+    m.nb = (int64_t)(g.W / g.B0) * (h0 / g.B0);
+    m.used = kind == kFrame && key_b(w.key) == key_a(w.key) + 1;
+    finalise_measure(m);
+    c->store.map[w.key] = m;
+    c->inflight.erase(w.key);
+    if (w.vec_off) {
+      const int a = key_a(w.key);
+      const size_t nbk = (size_t)(g.W / g.B0) * (g.H / g.B0);
+      if (c->stateless_) {
+        c->vec_out_.push_back({w.key, std::vector<short2>(h_vec.begin() + (w.vec_off - 1),
+                                                         h_vec.begin() + (w.vec_off - 1) + nbk)});
+      } else if (key_b(w.key) == a + 1) {
+        if (c->motion.size() < (size_t)(a + 1) * nbk * 2) c->motion.resize((size_t)(a + 1) * nbk * 2, 0);
+        for (size_t q = 0; q < nbk; q++) {
+          c->motion[(size_t)a * nbk * 2 + 2 * q] = h_vec[w.vec_off - 1 + q].x;
+          c->motion[(size_t)a * nbk * 2 + 2 * q + 1] = h_vec[w.vec_off - 1 + q].y;
+        }
+      }
+    }
+  }
+  // ---- detectors and eviction ---------------------------------------------------------
+  for (Clip* c : clips) {
+    if (c->status || c->stateless_ || c->done()) continue;
+    std::vector<uint64_t> need;
+    c->det.run(c->store, c->pushed, c->finished, need);
+    std::sort(need.begin(), need.end());
+    need.erase(std::unique(need.begin(), need.end()), need.end());
+    c->pending = need;
+    if (c->done() && c->t_done < 0) c->t_done = now_seconds();
+    const int keep = std::min(c->det.keep_from(), c->aon_next);
+    if (c->done()) c->evicted = c->pushed;
+    else c->evicted = std::max(c->evicted, std::min(keep, c->pushed));
+  }
+  return npairs + ndown;
+}
+
+int Engine::measure_pairs(int width, int height, const uint8_t* frames, long long pitch, long long stride,
+                          int nframes, const int* kinds, const int* ia, const int* ib, int npairs, int64_t* records,
+                          int16_t* motion, cudaStream_t st, std::string& why) {
+  int rc = validate_size(width, height, p, why);
+  if (rc) return rc;
+  if (!frames || nframes <= 0 || npairs < 0 || (npairs && (!kinds || !ia || !ib || !records))) {
+    why = "null pointer or empty frame set";
+    return ANALYSER_ERR_INVALID_ARG;
+  }
+  if (pitch < width || pitch % 16 || ((uintptr_t)frames % 16) || stride % 16 || stride < pitch * height) {
+    why = "device frames need 16-byte aligned base, pitch and stride, pitch >= width";
+    return ANALYSER_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < npairs; i++) {
+    if (kinds[i] < 0 || kinds[i] > 2 || ia[i] < 0 || ib[i] < 0 || ia[i] >= nframes || ib[i] >= nframes) {
+      why = "pair index or kind out of range";
+      return ANALYSER_ERR_INVALID_ARG;
+    }
+  }
+  Clip c;
+  c.geo.W = width;
+  c.geo.H = height;
+  c.cap = nframes;
+  c.stateless_ = true;
+  c.external_l0 = true;
+  c.want_vec_ = motion != nullptr;
+  cudaStream_t saved = stream;
+  if (st) stream = st;
+  rc = add_clip(&c, why, false);
+  if (rc) { stream = saved; return rc; }
+  attach_device(&c, frames, pitch, stride, nframes);
+  for (int i = 0; i < npairs; i++) c.pending.push_back(pair_key(kinds[i], ia[i], ib[i]));
+  rc = run_alone(&c);
+  if (c.d_ring) { cudaFree(c.d_ring); c.d_ring = nullptr; }
+  stream = saved;
+  if (rc < 0 || status) {
+    why = message;
+    int s = status ? status : rc;
+    status = ANALYSER_OK;
+    return s;
+  }
+  const int nbk = (width / c.geo.B0) * (height / c.geo.B0);
+  const int nbk_f = (width / c.geo.B0) * ((height / 2) / c.geo.B0);
+  size_t moff = 0;
+  for (int i = 0; i < npairs; i++) {
+    const uint64_t k = pair_key(kinds[i], ia[i], ib[i]);
+    Measure* m = c.store.find(kinds[i], ia[i], ib[i]);
+    for (int w = 0; w < kRecWords; w++) records[(size_t)kRecWords * i + w] = m->s[w];
+    if (motion) {
+      const int nb_here = kinds[i] == kFrame ? nbk : nbk_f;
+      for (auto& vo : c.vec_out_)
+        if (vo.first == k) {
+          for (int q = 0; q < nb_here && q < (int)vo.second.size(); q++) {
+            motion[moff + 2 * q] = vo.second[q].x;
+            motion[moff + 2 * q + 1] = vo.second[q].y;
+          }
+          break;
+        }
+      moff += (size_t)2 * nb_here;
+    }
+  }
+  return ANALYSER_OK;
+}
+
+void build_results(const Clip& c, ResultsBuf& out) {
+  const Detector& d = c.det;
+  out.cuts = d.cuts;
+  out.dissolves = d.dissolves;
+  out.keyframes = d.keyframes;
+  out.shots.clear();
+  for (const ShotOut& s : d.shots)
+    out.shots.push_back({s.first, s.last, s.label, s.field_order, s.phase, s.analysed});
+  std::map<uint64_t, const Measure*> ordered;
+  for (auto& kv : c.store.map)
+    if (kv.second.used) ordered[kv.first] = &kv.second;
+  out.measures.clear();
+  for (auto& kv : ordered) {
+    const Measure& m = *kv.second;
+    analyser_measure am;
+    am.kind = key_kind(kv.first);
+    am.a = key_a(kv.first);
+    am.b = key_b(kv.first);
+    am.si = m.s[0]; am.sj = m.s[1]; am.sii = m.s[2]; am.sjj = m.s[3]; am.sij = m.s[4]; am.sabs = m.s[5];
+    am.samm = m.s[6];
+    am.n = m.n; am.nb = m.nb;
+    am.ncc = m.ncc; am.swr = m.swr; am.amm = m.amm; am.act = m.act;
+    out.measures.push_back(am);
+  }
+  out.motion = c.motion;
+  analyser_results_t& r = out.r;
+  std::memset(&r, 0, sizeof(r));
+  r.nframes = c.pushed;
+  r.ncuts = (int)out.cuts.size(); r.cuts = out.cuts.data();
+  r.ndissolves = (int)out.dissolves.size() / 2; r.dissolves = out.dissolves.data();
+  r.nshots = (int)out.shots.size(); r.shots = out.shots.data();
+  r.label = d.clip_label; r.field_order = d.clip_fo; r.pulldown_phase = d.clip_phase;
+  r.nkeyframes = (int)out.keyframes.size(); r.keyframes = out.keyframes.data();
+  r.nmeasures = (int)out.measures.size(); r.measures = out.measures.data();
+  if (!out.motion.empty()) {
+    r.motion_w = c.geo.W / c.geo.B0;
+    r.motion_h = c.geo.H / c.geo.B0;
+    r.motion = out.motion.data();
+  }
+}
+
+}  // namespace va

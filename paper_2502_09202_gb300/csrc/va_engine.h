@@ -1,0 +1,152 @@
+// Runtime of the analyser: per-clip device windows, the measure cache and GPU
+// waves that batch the work of every active clip into one set of launches.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <unordered_set>
+#include <vector>
+
+#include "../../include/analyser.h"
+#include "va_detect.h"
+#include "va_kernels.cuh"
+
+namespace va {
+
+double now_seconds();
+int validate_params(const analyser_params& p, std::string& why);
+int validate_size(int width, int height, const analyser_params& p, std::string& why);
+
+// Level geometry of one clip.
+struct Geometry {
+  int W = 0, H = 0, L = 0, B0 = 0;
+  int fw[kMaxLevels], fh[kMaxLevels], fp[kMaxLevels];   // frame levels (fp[0] = ring pitch)
+  int gw[kMaxLevels], gh[kMaxLevels], gp[kMaxLevels];   // field levels
+  size_t off_f[kMaxLevels], off_u[kMaxLevels], off_l[kMaxLevels];  // offsets within a slot (levels >= 1)
+  size_t slot_bytes = 0;
+  size_t l0_bytes = 0;
+  void init(int width, int height, int levels, bool own_l0 = true);
+};
+
+// One clip being analysed.
+struct Clip {
+  long long id = 0;
+  Geometry geo;
+  double fps = 25.0;
+  analyser_params p{};
+  int tbx = 8, tby = 4;              // tile of the pair kernel (autotuned per resolution)
+  // device window
+  int cap = 0;                       // slots
+  uint8_t* d_ring = nullptr;         // cap * slot_bytes
+  std::vector<const uint8_t*> l0;    // level-0 frame of each slot
+  std::vector<int> l0_pitch;
+  bool external_l0 = false;          // slots point at caller device frames
+  // progress
+  int pushed = 0;        // frames [0, pushed) delivered
+  int pyr_done = 0;      // frames [0, pyr_done) have pyramids
+  int evicted = 0;       // frames [0, evicted) no longer resident
+  int aon_next = 0;      // next always-on pair (t, t+1) not yet requested
+  bool finished = false;
+  MeasureStore store;
+  Detector det;
+  std::vector<uint64_t> pending;     // requests for the next wave
+  std::unordered_set<uint64_t> inflight;
+  std::vector<int16_t> motion;       // level-0 fields of (t, t+1) when want_motion
+  int status = ANALYSER_OK;
+  std::string message;
+  // host frame source (server path)
+  const uint8_t* host_frames = nullptr;
+  long long host_pitch = 0;
+  int host_nframes = 0;
+  // timing (server path)
+  double t_submit = 0.0, t_done = -1.0;
+  // stateless measure calls: no detector, requested pairs only
+  bool stateless_ = false;
+  bool want_vec_ = false;
+  std::vector<std::pair<uint64_t, std::vector<short2>>> vec_out_;
+  bool done() const { return det.done(); }
+  int slot_of(int f) const { return f % cap; }
+  size_t device_bytes() const { return (size_t)cap * geo.slot_bytes; }
+};
+
+// Results kept for the C ABI.
+struct ResultsBuf {
+  std::vector<int> cuts, dissolves, keyframes;
+  std::vector<analyser_shot> shots;
+  std::vector<analyser_measure> measures;
+  std::vector<int16_t> motion;
+  analyser_results_t r{};
+};
+void build_results(const Clip& c, ResultsBuf& out);
+
+class Engine {
+ public:
+  explicit Engine(const analyser_params& p);
+  ~Engine();
+  int init(std::string& why);
+
+  // clip management
+  int add_clip(Clip* c, std::string& why, bool enlist = true);  // allocates the clip's ring
+  void remove_clip(Clip* c);
+  static size_t ring_bytes(const Geometry& g, int cap);
+
+  // copy host frames into a clip's free slots; returns frames taken
+  int upload_host(Clip* c, const uint8_t* frames, long long pitch, int nframes);
+  // reference device frames
+  int attach_device(Clip* c, const uint8_t* frames, long long pitch, long long stride, int nframes);
+
+  // One wave over all clips: pyramids of new frames, every requested pair,
+  // readback, detector advance, eviction.  Returns the number of pairs run
+  // (0 = nothing to do), or a negative error.
+  int wave();
+  int free_slots(const Clip* c) const { return c->cap - (c->pushed - c->evicted); }
+
+  // stateless measure for tests and timing
+  int measure_pairs(int width, int height, const uint8_t* frames, long long pitch, long long stride, int nframes,
+                    const int* kinds, const int* ia, const int* ib, int npairs, int64_t* records, int16_t* motion,
+                    cudaStream_t st, std::string& why);
+
+  // tile choice for a resolution (autotuned once per engine and size)
+  void choose_tile(int width, int height, int* tbx, int* tby);
+
+  analyser_params p;
+  std::vector<Clip*> clips;
+  cudaStream_t stream = nullptr;
+  long long n_pairs = 0, n_waves = 0, n_launches = 0;
+  int status = ANALYSER_OK;
+  std::string message;
+  bool autotune = true;
+
+ private:
+  int ensure_capacity(int npairs, int ndown);
+  int run_alone(Clip* c);
+  int setup_pair_job(const Clip& c, uint64_t key, PairJob& pj, int item_begin, unsigned long long* rec,
+                     short2* vec);
+
+  // device tables
+  uint32_t* d_qtab = nullptr;
+  int qmax = 0;
+  int* d_status = nullptr;
+  int* h_status = nullptr;
+  int sm_count = 0;
+  // wave buffers
+  int cap_pairs = 0, cap_down = 0;
+  PairJob* d_pjobs = nullptr;
+  PairJob* h_pjobs = nullptr;
+  DownJob* d_djobs = nullptr;
+  DownJob* h_djobs = nullptr;
+  unsigned long long* d_rec = nullptr;
+  unsigned long long* h_rec = nullptr;
+  short2* d_vec = nullptr;
+  size_t cap_vec = 0;
+  std::vector<short2> h_vec;
+  // per wave bookkeeping
+  struct WavePair { Clip* clip; uint64_t key; size_t vec_off; int tbx, tby; };
+  std::vector<WavePair> wp_;
+  std::vector<std::pair<int, int>> tune_keys_;
+  std::vector<std::pair<int, int>> tune_vals_;
+};
+
+}  // namespace va

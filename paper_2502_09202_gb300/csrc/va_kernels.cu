@@ -1,0 +1,408 @@
+// CUDA kernels of the analyser's hot path, written for sm_103a.
+//
+//   downsample_kernel  one pyramid level for a batch of planes (frames and fields)
+//   pair_kernel        one fused pass per (pair, tile of blocks):
+//                        coarse exhaustive block search on the coarsest level,
+//                        refinement at every finer level, AMM sum, motion-
+//                        compensated NCC sums and the absolute residual
+//
+// The arithmetic follows Sec. III.A of the paper (motion field, AMM, warped
+// NCC); the estimator is integer block matching on a box-filter pyramid
+// (the paper's own flow estimator is dense inverse search; block matching with
+// a motion cost is the reading implemented here and in the oracle).
+// All sums are exact integers; no floating point runs on the device.
+#include "va_kernels.cuh"
+
+namespace va {
+
+// ---------------------------------------------------------------------------
+// packed-byte primitives
+// ---------------------------------------------------------------------------
+
+// c + sum over the 4 bytes of |a_k - b_k|
+__device__ __forceinline__ uint32_t sad4(uint32_t a, uint32_t b, uint32_t c) {
+#if defined(VA_SAD_DP4A)
+  return __dp4a(__vabsdiffu4(a, b), 0x01010101u, c);
+#elif defined(VA_SAD_VSAD)
+  return __vsadu4(a, b) + c;
+#else
+  uint32_t d;
+  asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+#endif
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// 4 bytes of row `row` starting at column x (any alignment), read clamp-to-edge.
+__device__ __forceinline__ uint32_t load4_clamped(const uint8_t* row, int x, int w) {
+  uint32_t v = 0;
+#pragma unroll
+  for (int k = 0; k < 4; k++) v |= (uint32_t)row[clampi(x + k, 0, w - 1)] << (8 * k);
+  return v;
+}
+
+// 4 bytes at column x of a row whose start is 4-byte aligned, any x alignment;
+// the caller guarantees that bytes [x & ~3, (x & ~3) + 7] are readable.
+__device__ __forceinline__ uint32_t load4_unaligned(const uint8_t* row, int x) {
+  const uint32_t* p = reinterpret_cast<const uint32_t*>(row + (x & ~3));
+  const uint32_t lo = __ldg(p), hi = __ldg(p + 1);
+  return __funnelshift_r(lo, hi, 8 * (x & 3));
+}
+
+// ---------------------------------------------------------------------------
+// pyramid: dst(x, y) = (a + b + c + d + 2) >> 2 over src rows 2y, 2y+1, cols 2x, 2x+1
+// ---------------------------------------------------------------------------
+
+__global__ void downsample_kernel(const DownJob* __restrict__ jobs) {
+  const DownJob jb = jobs[blockIdx.z];
+  const int dw = jb.src.w / 2, dh = jb.src.h / 2;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int xg = blockIdx.x * blockDim.x + threadIdx.x;   // group of 4 output pixels
+  const int x = xg * 4;
+  if (y >= dh || x >= dw) return;
+  const uint8_t* r0 = jb.src.p + (size_t)(2 * y) * jb.src.pitch;
+  const uint8_t* r1 = r0 + jb.src.pitch;
+  uint8_t* out = jb.dst + (size_t)y * jb.dst_pitch;
+  if (x + 4 <= dw) {
+    // 8 source bytes per row; src views are 8-byte aligned at even x groups
+    const uint2 a = *reinterpret_cast<const uint2*>(r0 + 2 * x);
+    const uint2 c = *reinterpret_cast<const uint2*>(r1 + 2 * x);
+    const unsigned long long A = ((unsigned long long)a.y << 32) | a.x;
+    const unsigned long long C = ((unsigned long long)c.y << 32) | c.x;
+    const unsigned long long M = 0x00FF00FF00FF00FFull;
+    // 16-bit lanes: (a0 + a1 + c0 + c1 + 2) for each of the 4 output pixels
+    const unsigned long long s = (A & M) + ((A >> 8) & M) + (C & M) + ((C >> 8) & M) + 0x0002000200020002ull;
+    const unsigned long long q = (s >> 2) & M;
+    const uint32_t lo = (uint32_t)q, hi = (uint32_t)(q >> 32);
+    *reinterpret_cast<uint32_t*>(out + x) = __byte_perm(lo, hi, 0x6420);
+  } else {
+    for (int k = x; k < dw; k++) {
+      const int s = r0[2 * k] + r0[2 * k + 1] + r1[2 * k] + r1[2 * k + 1] + 2;
+      out[k] = (uint8_t)(s >> 2);
+    }
+  }
+}
+
+cudaError_t launch_downsample(const DownJob* d_jobs, int njobs, int max_dst_h, int max_dst_w, cudaStream_t st) {
+  if (njobs <= 0) return cudaSuccess;
+  dim3 blk(32, 8);
+  dim3 grd((max_dst_w / 4 + 1 + blk.x - 1) / blk.x, (max_dst_h + blk.y - 1) / blk.y, njobs);
+  downsample_kernel<<<grd, blk, 0, st>>>(d_jobs);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// fused pair kernel
+// ---------------------------------------------------------------------------
+
+template <int R, int TBX, int TBY>
+struct PairShape {
+  static constexpr int G = (2 * R + 4) / 4;       // vx groups of 4 candidates
+  static constexpr int NB = TBX * TBY;            // blocks per tile
+  static constexpr int NA = NB * G;               // threads busy in the coarse phase
+  static constexpr int NT = (NA + 31) / 32 * 32;  // threads (whole warps)
+  static constexpr int WROWS = TBY * kCoarseSide + 2 * R;
+  static constexpr int WWORDS = TBX + G;
+  static constexpr int NW = (NT + 31) / 32;
+};
+
+template <int R, int TBX, int TBY>
+__global__ void __launch_bounds__(PairShape<R, TBX, TBY>::NT)
+pair_kernel(const PairBatch b) {
+  using S = PairShape<R, TBX, TBY>;
+  constexpr int G = S::G, NB = S::NB, NT = S::NT, WROWS = S::WROWS, WWORDS = S::WWORDS;
+  static_assert(R % 4 == 0 && R <= 31, "coarse radius");
+
+  __shared__ uint32_t s_jwin[WROWS][WWORDS];
+  __shared__ uint32_t s_iw[TBY * kCoarseSide][TBX];
+  __shared__ uint32_t s_best32[NB];
+  __shared__ unsigned long long s_best64[NB];
+  __shared__ int s_vx[NB], s_vy[NB];
+  __shared__ unsigned long long s_red[S::NW][kRecWords];
+  __shared__ PairJob s_job;
+
+  const int tid = threadIdx.x;
+  const int L = b.cfg.levels;
+  const int B0 = kCoarseSide << (L - 1);
+  const int lam = b.cfg.lambda;
+  const int rr = b.cfg.refine;
+  const int side = 2 * rr + 1, ncand = side * side;
+
+  for (int item = blockIdx.x; item < b.nitems; item += gridDim.x) {
+    // ---- locate the job owning this tile ------------------------------------
+    int lo = 0, hi = b.njobs - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (b.jobs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+    }
+    {
+      static_assert(sizeof(PairJob) % 4 == 0, "job copy");
+      const int* src = reinterpret_cast<const int*>(b.jobs + lo);
+      int* dst = reinterpret_cast<int*>(&s_job);
+      for (int i = tid; i < (int)(sizeof(PairJob) / 4); i += NT) dst[i] = src[i];
+    }
+    __syncthreads();
+    const PairJob& jb = s_job;
+    const int local = item - jb.item_begin;
+    const int bx0 = (local % jb.tiles_x) * TBX, by0 = (local / jb.tiles_x) * TBY;
+    const int nbx = jb.nbx, nby = jb.nby;
+
+    // ---- phase A: exhaustive search on the coarsest level --------------------
+    {
+      const Plane I2 = jb.I[L - 1], J2 = jb.J[L - 1];
+      const int Xw0 = bx0 * kCoarseSide - R, Yw0 = by0 * kCoarseSide - R;
+      for (int idx = tid; idx < WROWS * WWORDS; idx += NT) {
+        const int wy = idx / WWORDS, wx = idx - wy * WWORDS;
+        const int y = clampi(Yw0 + wy, 0, J2.h - 1);
+        const int x = Xw0 + 4 * wx;
+        const uint8_t* row = J2.p + (size_t)y * J2.pitch;
+        uint32_t v;
+        if (x >= 0 && x + 3 <= J2.w - 1) v = __ldg(reinterpret_cast<const uint32_t*>(row + x));
+        else v = load4_clamped(row, x, J2.w);
+        s_jwin[wy][wx] = v;
+      }
+      for (int idx = tid; idx < TBY * kCoarseSide * TBX; idx += NT) {
+        const int ry = idx / TBX, wx = idx - ry * TBX;
+        uint32_t v = 0;
+        if (bx0 + wx < nbx && by0 + ry / kCoarseSide < nby)
+          v = __ldg(reinterpret_cast<const uint32_t*>(I2.p + (size_t)(by0 * kCoarseSide + ry) * I2.pitch +
+                                                      (bx0 + wx) * kCoarseSide));
+        s_iw[ry][wx] = v;
+      }
+      for (int i = tid; i < NB; i += NT) s_best32[i] = 0xFFFFFFFFu;
+      __syncthreads();
+
+      const bool in_a = tid < S::NA;
+      const int g = tid % G, bl = in_a ? tid / G : 0;
+      const int bxl = bl % TBX, byl = bl / TBX;
+      const bool active = in_a && (bx0 + bxl < nbx) && (by0 + byl < nby);
+      const uint32_t i0 = s_iw[byl * 4 + 0][bxl], i1 = s_iw[byl * 4 + 1][bxl];
+      const uint32_t i2 = s_iw[byl * 4 + 2][bxl], i3 = s_iw[byl * 4 + 3][bxl];
+      const uint32_t lam18 = (uint32_t)lam << 18;
+      uint32_t acc[4][4];
+      uint32_t best[4];
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        best[j] = 0xFFFFFFFFu;
+#pragma unroll
+        for (int k = 0; k < 4; k++) acc[j][k] = 0;
+      }
+      const uint32_t* wrow = &s_jwin[byl * 4][bxl + g];
+#pragma unroll
+      for (int dy = 0; dy < 2 * R + 4; dy++) {
+        const uint32_t wlo = wrow[dy * WWORDS], whi = wrow[dy * WWORDS + 1];
+        uint32_t w[4];
+        w[0] = wlo;
+        w[1] = __funnelshift_r(wlo, whi, 8);
+        w[2] = __funnelshift_r(wlo, whi, 16);
+        w[3] = __funnelshift_r(wlo, whi, 24);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          acc[j][0] = sad4(i0, w[j], acc[j][0]);
+          acc[j][1] = sad4(i1, w[j], acc[j][1]);
+          acc[j][2] = sad4(i2, w[j], acc[j][2]);
+          acc[j][3] = sad4(i3, w[j], acc[j][3]);
+        }
+        if (dy >= 3) {
+          const int vy = dy - R - 3;
+          const int avy = vy < 0 ? -vy : vy;
+          const uint32_t bv = lam18 * (uint32_t)avy + (((uint32_t)avy << 12) | ((uint32_t)(vy + R) << 6));
+#pragma unroll
+          for (int j = 0; j < 4; j++) best[j] = min(best[j], (acc[j][3] << 18) + bv);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          acc[j][3] = acc[j][2];
+          acc[j][2] = acc[j][1];
+          acc[j][1] = acc[j][0];
+          acc[j][0] = 0;
+        }
+      }
+      uint32_t tbest = 0xFFFFFFFFu;
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const int vx = -R + 4 * g + j;
+        if (vx <= R) {
+          const int avx = vx < 0 ? -vx : vx;
+          const uint32_t a = (((uint32_t)(lam * avx)) << 18) + ((uint32_t)avx << 12) + (uint32_t)(vx + R);
+          tbest = min(tbest, best[j] + a);
+        }
+      }
+      if (active) atomicMin(&s_best32[bl], tbest);
+      __syncthreads();
+      for (int i = tid; i < NB; i += NT) {
+        const uint32_t k = s_best32[i];
+        s_vx[i] = (int)(k & 63u) - R;
+        s_vy[i] = (int)((k >> 6) & 63u) - R;
+      }
+      __syncthreads();
+    }
+
+    // ---- phase B: refinement at levels L-2 .. 0 -------------------------------
+    for (int l = L - 2; l >= 0; l--) {
+      const Plane Il = jb.I[l], Jl = jb.J[l];
+      const int s = B0 >> l;
+      const int lim_w = min(Jl.w, Jl.pitch);
+      for (int i = tid; i < NB; i += NT) s_best64[i] = ~0ull;
+      __syncthreads();
+      for (int t = tid; t < NB * ncand; t += NT) {
+        const int bl = t / ncand, c = t - bl * ncand;
+        const int bxl = bl % TBX, byl = bl / TBX;
+        const int bx = bx0 + bxl, by = by0 + byl;
+        if (bx >= nbx || by >= nby) continue;
+        const int vx = 2 * s_vx[bl] + (c % side) - rr;
+        const int vy = 2 * s_vy[bl] + (c / side) - rr;
+        const int x0 = bx * s, y0 = by * s;
+        const int xj = x0 + vx;
+        const bool fast = (xj >= 0) && (xj + s + 3 <= lim_w - 1) && (y0 + vy >= 0) && (y0 + vy + s - 1 <= Jl.h - 1);
+        uint32_t sad = 0;
+        for (int y = 0; y < s; y++) {
+          const uint8_t* irow = Il.p + (size_t)(y0 + y) * Il.pitch + x0;
+          const int yj = clampi(y0 + y + vy, 0, Jl.h - 1);
+          const uint8_t* jrow = Jl.p + (size_t)yj * Jl.pitch;
+          for (int x = 0; x < s; x += 4) {
+            const uint32_t iv = __ldg(reinterpret_cast<const uint32_t*>(irow + x));
+            const uint32_t jv = fast ? load4_unaligned(jrow, xj + x) : load4_clamped(jrow, xj + x, Jl.w);
+            sad = sad4(iv, jv, sad);
+          }
+        }
+        const int n1 = abs(vx) + abs(vy);
+        const unsigned long long key = ((unsigned long long)(sad + (uint32_t)(lam * n1)) << 32) |
+                                       ((unsigned long long)n1 << 20) | ((unsigned long long)(vy + 512) << 10) |
+                                       (unsigned long long)(vx + 512);
+        atomicMin(&s_best64[bl], key);
+      }
+      __syncthreads();
+      for (int i = tid; i < NB; i += NT) {
+        const unsigned long long k = s_best64[i];
+        if (k != ~0ull) {
+          s_vx[i] = (int)(k & 1023ull) - 512;
+          s_vy[i] = (int)((k >> 10) & 1023ull) - 512;
+        }
+      }
+      __syncthreads();
+    }
+
+    // ---- phase C: AMM sum and motion-compensated sums over the tile's pixels --
+    {
+      const Plane I0 = jb.I[0], J0 = jb.J[0];
+      const int W = I0.w, H = I0.h;
+      const int xs = bx0 * B0, ys = by0 * B0;
+      const int xe = (bx0 + TBX >= nbx) ? W : (bx0 + TBX) * B0;
+      const int ye = (by0 + TBY >= nby) ? H : (by0 + TBY) * B0;
+      const int nwx = (xe - xs + 3) >> 2;
+      const int nrows = ye - ys;
+      const int lim_w = min(J0.w, J0.pitch);
+      uint32_t si = 0, sj = 0, sii = 0, sjj = 0, sij = 0, sab = 0;
+      for (int idx = tid; idx < nrows * nwx; idx += NT) {
+        const int ry = idx / nwx, wx = idx - ry * nwx;
+        const int y = ys + ry, x = xs + 4 * wx;
+        const int bx = min(x / B0, nbx - 1), by = min(y / B0, nby - 1);
+        const int bl = (by - by0) * TBX + (bx - bx0);
+        const int vx = s_vx[bl], vy = s_vy[bl];
+        const uint8_t* irow = I0.p + (size_t)y * I0.pitch;
+        const int yj = clampi(y + vy, 0, H - 1);
+        const uint8_t* jrow = J0.p + (size_t)yj * J0.pitch;
+        const int xj = x + vx;
+        uint32_t iv, jv;
+        if (x + 3 <= W - 1) {
+          iv = __ldg(reinterpret_cast<const uint32_t*>(irow + x));
+          jv = (xj >= 0 && xj + 7 <= lim_w - 1) ? load4_unaligned(jrow, xj) : load4_clamped(jrow, xj, J0.w);
+        } else {
+          // ragged right edge: bytes beyond W contribute zero to every sum
+          iv = 0; jv = 0;
+          for (int k = 0; x + k < W; k++) {
+            iv |= (uint32_t)irow[x + k] << (8 * k);
+            jv |= (uint32_t)jrow[clampi(xj + k, 0, W - 1)] << (8 * k);
+          }
+        }
+        si = __dp4a(iv, 0x01010101u, si);
+        sj = __dp4a(jv, 0x01010101u, sj);
+        sii = __dp4a(iv, iv, sii);
+        sjj = __dp4a(jv, jv, sjj);
+        sij = __dp4a(iv, jv, sij);
+        sab = sad4(iv, jv, sab);
+      }
+      // AMM: one term per block of the tile, from the exact table
+      uint32_t samm = 0;
+      for (int i = tid; i < NB; i += NT) {
+        const int bx = bx0 + i % TBX, by = by0 + i / TBX;
+        if (bx < nbx && by < nby) {
+          const int vx = s_vx[i], vy = s_vy[i];
+          const int k = vx * vx + vy * vy;
+          if (k <= b.qmax) samm += b.qtab[k];
+          else atomicOr(b.status, 1);
+          if (jb.vec) jb.vec[(size_t)by * nbx + bx] = make_short2((short)vx, (short)vy);
+        }
+      }
+      unsigned long long v[kRecWords] = {si, sj, sii, sjj, sij, sab, samm};
+#pragma unroll
+      for (int k = 0; k < kRecWords; k++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xFFFFFFFFu, v[k], o);
+      }
+      const int warp = tid >> 5, lane = tid & 31;
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < kRecWords; k++) s_red[warp][k] = v[k];
+      }
+      __syncthreads();
+      if (tid < kRecWords) {
+        unsigned long long a = 0;
+        for (int w = 0; w < S::NW; w++) a += s_red[w][tid];
+        atomicAdd(jb.rec + tid, a);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// dispatch over the compiled (radius, tile) variants
+// ---------------------------------------------------------------------------
+
+#define VA_TILES(X, R) X(R, 8, 4) X(R, 4, 4) X(R, 8, 2) X(R, 16, 2) X(R, 4, 8)
+#define VA_RADII(X) VA_TILES(X, 8) VA_TILES(X, 16) VA_TILES(X, 24)
+
+bool pair_tile_supported(int radius, int tbx, int tby) {
+#define VA_CASE(R_, X_, Y_) if (radius == R_ && tbx == X_ && tby == Y_) return true;
+  VA_RADII(VA_CASE)
+#undef VA_CASE
+  return false;
+}
+
+int pair_threads(int radius, int tbx, int tby) {
+#define VA_CASE(R_, X_, Y_) if (radius == R_ && tbx == X_ && tby == Y_) return PairShape<R_, X_, Y_>::NT;
+  VA_RADII(VA_CASE)
+#undef VA_CASE
+  return 0;
+}
+
+int pair_blocks_per_sm(int radius, int tbx, int tby) {
+  int n = 0;
+#define VA_CASE(R_, X_, Y_)                                                                        \
+  if (radius == R_ && tbx == X_ && tby == Y_) {                                                    \
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_kernel<R_, X_, Y_>,                 \
+                                                      PairShape<R_, X_, Y_>::NT, 0) != cudaSuccess) \
+      n = 1;                                                                                       \
+    return n;                                                                                      \
+  }
+  VA_RADII(VA_CASE)
+#undef VA_CASE
+  return 1;
+}
+
+cudaError_t launch_pairs(const PairBatch& b, int tbx, int tby, int grid, cudaStream_t st) {
+  if (b.nitems <= 0) return cudaSuccess;
+#define VA_CASE(R_, X_, Y_)                                                           \
+  if (b.cfg.radius == R_ && tbx == X_ && tby == Y_) {                                 \
+    pair_kernel<R_, X_, Y_><<<grid, PairShape<R_, X_, Y_>::NT, 0, st>>>(b);           \
+    return cudaGetLastError();                                                        \
+  }
+  VA_RADII(VA_CASE)
+#undef VA_CASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace va

@@ -1,0 +1,62 @@
+// Device-side data structures shared by the kernels and the host engine.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace va {
+
+constexpr int kMaxLevels = 4;
+constexpr int kCoarseSide = 4;     // block side at the coarsest pyramid level
+constexpr int kRecWords = 7;       // sum i, sum j, sum i^2, sum j^2, sum i*j, sum |i-j|, S_amm
+
+// One 8-bit image plane (or a row-strided view of one, e.g. a field).
+struct Plane {
+  const uint8_t* p;
+  int pitch;   // bytes between consecutive rows of this view
+  int w, h;
+};
+
+// One downsampling step: dst = box-filter of src, dims floor(w/2) x floor(h/2).
+struct DownJob {
+  Plane src;
+  uint8_t* dst;
+  int dst_pitch;
+};
+
+// One pair measure: I against J (both views have the same dims per level).
+struct PairJob {
+  Plane I[kMaxLevels];
+  Plane J[kMaxLevels];
+  int nbx, nby;              // level-0 block grid
+  int tiles_x, tiles_y;      // tile grid over the block grid
+  int item_begin;            // index of this job's first tile in the batch
+  unsigned long long* rec;   // kRecWords accumulators (zeroed before the launch)
+  short2* vec;               // optional level-0 motion field dump (nby*nbx), or null
+};
+
+struct SearchCfg {
+  int levels;    // L; level-0 block side is kCoarseSide << (L-1)
+  int radius;    // coarse exhaustive radius R (multiple of 4)
+  int refine;    // refinement radius r
+  int lambda;    // motion cost per pixel of |vx|+|vy|
+};
+
+struct PairBatch {
+  const PairJob* jobs;
+  int njobs;
+  int nitems;                // total tiles over all jobs
+  const uint32_t* qtab;      // Q(k) = floor(sqrt(k) * 2^16), k = 0..qmax
+  int qmax;
+  SearchCfg cfg;
+  int* status;               // error word: nonzero when a device-side check failed
+};
+
+// Host launchers (defined in va_kernels.cu).
+cudaError_t launch_downsample(const DownJob* d_jobs, int njobs, int max_dst_h, int max_dst_w,
+                              cudaStream_t st);
+cudaError_t launch_pairs(const PairBatch& b, int tbx, int tby, int grid, cudaStream_t st);
+bool pair_tile_supported(int radius, int tbx, int tby);
+int pair_threads(int radius, int tbx, int tby);
+int pair_blocks_per_sm(int radius, int tbx, int tby);
+
+}  // namespace va

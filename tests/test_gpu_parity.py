@@ -1,0 +1,199 @@
+"""GPU path vs oracle, through the C ABI: bit-exact motion vectors, integer sums,
+FP64 measures and decisions."""
+import numpy as np
+import pytest
+
+from oracle import analyser as OA
+from oracle import measures as OM
+from paper_2502_09202_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REC7 = ("si", "sj", "sii", "sjj", "sij", "sabs", "samm")
+
+
+def _api():
+    from paper_2502_09202_gb300 import api
+    return api
+
+
+def _dev(frames: np.ndarray, pad: int = 0):
+    """Device copy (n, h, w) with rows padded to a multiple of 64 + pad bytes."""
+    n, h, w = frames.shape
+    pitch = (w + 63) // 64 * 64 + pad
+    buf = torch.zeros((n, h, pitch), dtype=torch.uint8, device="cuda")
+    buf[:, :, :w] = torch.from_numpy(frames).cuda()
+    return buf[:, :, :w]
+
+
+def _oracle_pair(kind, fa, fb, sp=OM.SearchParams()):
+    I, J = OM.pair_images(kind, fa, fb)
+    return OM.pair_record(I, J, sp, want_vec=True)
+
+
+@pytest.mark.parametrize("w,h", [(200, 136), (333, 190), (640, 360), (1100, 258)])
+def test_measure_pairs_bit_exact_random_content(w, h):
+    """Pairs of every kind on sizes that span several tiles and ragged tails."""
+    api = _api()
+    clip = synth.Clip(synth.ClipSpec(w, h, 6, 25.0, synth.TFF, 5, 3.0,
+                                     synth.SceneStyle(n_objects=(4, 6), obj_speed=12, cell=8, bg_kind="textured")))
+    frames = clip.frames()
+    kinds = [0, 0, 1, 1, 2, 0, 0]
+    ia = [0, 1, 2, 3, 4, 5, 0]
+    ib = [1, 2, 2, 4, 5, 0, 5]
+    rec, mot = api.measure_pairs(_dev(frames), kinds, ia, ib, want_motion=True)
+    for k in range(len(kinds)):
+        ref, vec = _oracle_pair(kinds[k], frames[ia[k]], frames[ib[k]])
+        assert list(rec[k]) == [ref[f] for f in REC7], (k, list(rec[k]), ref)
+        assert np.array_equal(mot[k], vec), k
+
+
+@pytest.mark.parametrize("tile", [(8, 4), (4, 4), (8, 2), (16, 2), (4, 8)])
+def test_every_tile_shape_gives_identical_results(tile):
+    api = _api()
+    frames = synth.Clip(synth.config_small()).frames(18, 23)
+    ia, ib = [0, 1, 2, 3, 0], [1, 2, 3, 4, 4]
+    rec, mot = api.measure_pairs(_dev(frames), [0, 0, 0, 0, 2], ia, ib, want_motion=True,
+                                 tile_x=tile[0], tile_y=tile[1])
+    for k in range(5):
+        ref, vec = _oracle_pair(2 if k == 4 else 0, frames[ia[k]], frames[ib[k]])
+        assert list(rec[k]) == [ref[f] for f in REC7]
+        assert np.array_equal(mot[k], vec)
+
+
+@pytest.mark.parametrize("sx,sy", [(0, 0), (12, -8), (-40, 28), (64, 0)])
+def test_known_shift_and_identity(sx, sy):
+    api = _api()
+    I, J = synth.shifted_pair(31, 256, 192, sx, sy)
+    frames = np.stack([I, J])
+    rec, mot = api.measure_pairs(_dev(frames), [0, 0], [0, 0], [1, 0], want_motion=True)
+    ref, vec = _oracle_pair(0, I, J)
+    assert list(rec[0]) == [ref[f] for f in REC7]
+    assert np.array_equal(mot[0], vec)
+    assert (mot[1] == 0).all() and rec[1][5] == 0           # identical pair: zero field, zero residual
+
+
+def test_degenerate_flat_frames_and_extremes():
+    api = _api()
+    flat0 = np.zeros((96, 128), np.uint8)
+    flat255 = np.full((96, 128), 255, np.uint8)
+    tex = synth.random_frame(8, 128, 96)
+    frames = np.stack([flat0, flat255, tex])
+    kinds, ia, ib = [0, 0, 0, 1, 2], [0, 0, 2, 1, 2], [1, 2, 0, 2, 0]
+    rec, mot = api.measure_pairs(_dev(frames, pad=16), kinds, ia, ib, want_motion=True)
+    for k in range(len(kinds)):
+        ref, vec = _oracle_pair(kinds[k], frames[ia[k]], frames[ib[k]])
+        assert list(rec[k]) == [ref[f] for f in REC7]
+        assert np.array_equal(mot[k], vec)
+
+
+def _compare_results(got, ref):
+    for k in ("cuts", "dissolves", "keyframes", "shots", "label", "field_order", "pulldown_phase"):
+        assert got[k] == ref[k], (k, got[k], ref[k])
+    assert set(got["measures"]) == set(ref["measures"])
+    for key, m in ref["measures"].items():
+        g = got["measures"][key]
+        for f, v in m.items():
+            # integer sums and decisions bit-exact; FP64 values formed by the same
+            # IEEE operations on both sides: identical (bound stated: 1e-9)
+            assert g[f] == v, (key, f, g[f], v)
+
+
+def test_small_clip_end_to_end_host_push():
+    api = _api()
+    spec = synth.config_small()
+    frames = synth.Clip(spec).frames()
+    with api.Analyser(spec.width, spec.height, spec.fps) as a:
+        a.push(frames[:10])
+        a.push(frames[10:37])
+        a.push(frames[37:])
+        a.finish()
+        got = a.results()
+    _compare_results(got, OA.analyse_frames(frames))
+
+
+def test_small_clip_device_push_and_small_window():
+    api = _api()
+    spec = synth.config_small()
+    frames = synth.Clip(spec).frames()
+    with api.Analyser(spec.width, spec.height, spec.fps, window_frames=22) as a:
+        a.push_device(_dev(frames))
+        a.finish()
+        got = a.results()
+    _compare_results(got, OA.analyse_frames(frames))
+
+
+def test_motion_dump_matches_oracle():
+    api = _api()
+    spec = synth.config_small()
+    frames = synth.Clip(spec).frames(0, 12)
+    with api.Analyser(spec.width, spec.height, spec.fps, want_motion=1) as a:
+        a.push(frames)
+        a.finish()
+        got = a.results()
+    for t in range(11):
+        _, vec = _oracle_pair(0, frames[t], frames[t + 1])
+        assert np.array_equal(got["motion"][t], vec), t
+
+
+def test_empty_and_tiny_clips():
+    api = _api()
+    for n in (0, 1, 2, 3):
+        frames = synth.Clip(synth.config_small()).frames(0, n)
+        with api.Analyser(320, 180, 25.0) as a:
+            if n:
+                a.push(frames)
+            a.finish()
+            got = a.results()
+        ref = OA.analyse_frames(frames) if n else OA.OracleAnalyser(lambda t: None, 0).run()
+        _compare_results(got, ref)
+
+
+def test_reduced_interlaced_and_pulldown_clips():
+    """Configs 2 and 3 at reduced size (same structure and motion) end to end."""
+    api = _api()
+    for spec in (synth.config_interlaced(nframes=180, width=640, height=360),
+                 synth.config_pulldown(nframes=160, width=640, height=360)):
+        frames = synth.Clip(spec).frames()
+        with api.Analyser(spec.width, spec.height, spec.fps) as a:
+            a.push(frames)
+            a.finish()
+            got = a.results()
+        _compare_results(got, OA.analyse_frames(frames))
+
+
+def test_server_results_identical_alone_and_in_the_mix():
+    api = _api()
+    specs = [synth.config_small(), synth.config_interlaced(nframes=40, width=256, height=144),
+             synth.config_pulldown(nframes=36, width=384, height=216)]
+    clips = [synth.Clip(s).frames() for s in specs]
+    alone = []
+    for s, f in zip(specs, clips):
+        with api.Analyser(s.width, s.height, s.fps) as a:
+            a.push(f)
+            a.finish()
+            alone.append(a.results())
+    srv = api.Server(budget_bytes=8 << 30)
+    tickets = [srv.submit(f, s.fps) for s, f in zip(specs, clips)]
+    srv.drain()
+    for t, ref in zip(tickets, alone):
+        _compare_results(srv.poll(t), ref)
+        assert srv.latency(t) >= 0.0
+    srv.close()
+
+
+def test_full_size_1080p_sampled_pairs():
+    """At the benchmark's 1080p size and launch configuration: sampled pairs of
+    every kind, compared value by value with the oracle."""
+    api = _api()
+    spec = synth.config_interlaced()
+    clip = synth.Clip(spec)
+    ts = [0, 1, 2, 211, 212, 219]
+    frames = np.stack([clip.frame(t) for t in ts])
+    kinds, ia, ib = [0, 0, 1, 1, 2, 0], [0, 1, 0, 0, 0, 3], [1, 2, 0, 1, 1, 5]
+    rec, mot = api.measure_pairs(_dev(frames), kinds, ia, ib, want_motion=True)
+    for k in range(len(kinds)):
+        ref, vec = _oracle_pair(kinds[k], frames[ia[k]], frames[ib[k]])
+        assert list(rec[k]) == [ref[f] for f in REC7]
+        assert np.array_equal(mot[k], vec)
