@@ -1,0 +1,313 @@
+"""Benchmark: frames/s (and x real time) of the analyser on the 1080p interlaced
+workload (1920x1080, 1500 frames, 25 fps, top field first, cuts, 8-frame
+dissolves, flashes; seeded synthetic video).
+
+One step = one full analysis of the clip: pyramids, every always-on pair,
+every deep-check and field pair the detectors request, all decisions.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  `value` is frames/s with the clip resident in HBM
+(analyser_push_frames_device); `e2e` is the same metric through
+analyser_push_frames from pinned host memory.  `--impl reference` times the
+CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "interlaced-tff-1920x1080x1500@25fps"
+METRIC = "frames/s at 1080p luma (full analysis: measures + decisions)"
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _spec():
+    from paper_2502_09202_gb300 import synth
+    return synth.config_interlaced()
+
+
+def _make_frames(spec, rank: int):
+    """Synthetic clip as a (T, H, W) uint8 host array; generated with a process pool."""
+    import numpy as np
+    from concurrent.futures import ProcessPoolExecutor
+    import multiprocessing as mp
+    out = np.empty((spec.nframes, spec.height, spec.width), np.uint8)
+    chunk = 50
+    jobs = [(spec, s, min(s + chunk, spec.nframes)) for s in range(0, spec.nframes, chunk)]
+    with ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 4), mp_context=mp.get_context("spawn")) as ex:
+        for (s, e), arr in zip([(j[1], j[2]) for j in jobs], ex.map(_gen_chunk, jobs)):
+            out[s:e] = arr
+    return out
+
+
+def _gen_chunk(args):
+    spec, s, e = args
+    from paper_2502_09202_gb300 import synth
+    return synth.Clip(spec).frames(s, e)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                for line in out.stdout.strip().splitlines():
+                    self.samples.append([x.strip() for x in line.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            for i, n in enumerate(names):
+                if len(s) > 5 + i and s[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# measured peak of the packed-SAD sequence the kernels use (vabsdiff4 with accumulate),
+# from the microbenchmark recorded under profiles/: |a-b| accumulates per second
+SAD_PEAK_TABS = 83.42
+
+
+def cpu_baseline(spec, nframes_sample: int = 16, start: int = 300):
+    """The oracle as it stands on this host's cores: a bounded sample of the clip
+    (always-on pairs over a spawn-started pool, then the sequential detectors)."""
+    import multiprocessing as mp
+    from oracle import analyser as OA
+    from paper_2502_09202_gb300 import synth
+    cores = os.cpu_count() or 1
+    clip = synth.Clip(spec)
+    t0 = time.perf_counter()
+    # the sample: frames [start, start + n) of the workload, analysed as a clip
+    frames = [clip.frame(t) for t in range(start, start + nframes_sample)]
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    jobs = [(i, frames[i], frames[i + 1]) for i in range(nframes_sample - 1)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_pair_job, jobs)
+    pre = {(0, i, i + 1): r for i, r in res}
+    OA.OracleAnalyser(lambda t: frames[t], nframes_sample, OA.Params(), precomputed=pre).run()
+    dt = time.perf_counter() - t0
+    del t_gen
+    return {"value": nframes_sample / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"frames {start}..{start + nframes_sample - 1} of the workload analysed as one clip "
+                      f"({dt:.1f} s; always-on pairs over {cores} processes, detectors sequential)"}
+
+
+def _oracle_pair_job(args):
+    i, fa, fb = args
+    from oracle import measures as OM
+    return i, OM.measure(OM.FRAME, fa, fb)
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    spec = _spec()
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(spec, nframes_sample=args.ref_frames, start=300 + 20 * i)
+        if i >= args.warmup:
+            vals.append(r["value"])
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * args.ref_frames / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_frames": args.ref_frames},
+            "cpu_baseline": {**r, "value": v},
+            "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    rank, world, local = _env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2502_09202_gb300 import api
+
+    spec = _spec()
+    # every rank analyses its own copy of the clip (clips are independent: weak scaling, no collective)
+    host = _make_frames(spec, rank)
+    T, H, W = host.shape
+    pinned = torch.from_numpy(host).pin_memory()
+    dev = pinned.to(f"cuda:{local}", non_blocking=False)
+    torch.cuda.synchronize()
+
+    def one_step_device(time_kernels=0):
+        a = api.Analyser(W, H, spec.fps, device=local, time_kernels=time_kernels, window_frames=args.window)
+        a.push_device(dev)
+        a.finish()
+        res = a.results()
+        prof = a.profile()
+        a.close()
+        return res, prof
+
+    def one_step_host():
+        a = api.Analyser(W, H, spec.fps, device=local, window_frames=args.window)
+        a.push_host_ptr(pinned.data_ptr(), W, T)
+        a.finish()
+        res = a.results()
+        prof = a.profile()
+        a.close()
+        return res, prof
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        one_step_device()
+    stream = torch.cuda.current_stream()
+    # --- device-resident timing ---------------------------------------------------------
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    profs = []
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            res, prof = one_step_device(time_kernels=1)
+            profs.append(prof)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * T / (ms / 1000.0)
+
+    # --- end to end through host buffers --------------------------------------------------
+    for _ in range(max(1, args.warmup // 2)):
+        one_step_host()
+    barrier()
+    torch.cuda.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    hprofs = []
+    for _ in range(args.steps):
+        hres, hprof = one_step_host()
+        hprofs.append(hprof)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = e2.elapsed_time(e3) / args.steps
+    e2e_value = world * T / (ms_e2e / 1000.0)
+
+    # roofline of the dominant kernel (fused pair kernel): algorithmic |a-b| accumulates per launch
+    pair_ms = sum(p["pair_kernel_ms"] for p in profs)
+    pair_launches = sum(p["pair_launches"] for p in profs)
+    ops = sum(p["absdiff_ops"] for p in profs)
+    achieved = ops / (pair_ms / 1000.0) / 1e12 if pair_ms > 0 else None
+    pyr_ms = sum(p["pyramid_kernel_ms"] for p in profs)
+    launches = int(sum(p["launches"] for p in profs) / args.steps)
+    peaks = _peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "x_realtime": value / spec.fps,
+        "config": {"workload": WORKLOAD, "frames": T, "width": W, "height": H, "fps": spec.fps,
+                   "parallelism": f"replicas{world}", "l2": "inputs (3.1 GB per step) larger than L2",
+                   "window_frames": args.window, "pairs_per_step": profs[-1]["pairs"], "waves_per_step": profs[-1]["waves"],
+                   "cuts": res["cuts"], "dissolves": res["dissolves"], "label": res["label"]},
+        "e2e": {"value": e2e_value, "unit": "frames/s", "ms_per_step": ms_e2e,
+                "h2d_bytes_per_step": int(hprofs[-1]["h2d_bytes"]), "d2h_bytes_per_step": int(hprofs[-1]["d2h_bytes"])},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": "pair_kernel", "achieved": achieved, "peak": SAD_PEAK_TABS,
+                     "unit": "T|a-b|/s", "frac": (achieved / SAD_PEAK_TABS) if achieved else None,
+                     "traffic": None, "launches_per_step": pair_launches / args.steps,
+                     "kernel_ms_per_step": pair_ms / args.steps, "pyramid_ms_per_step": pyr_ms / args.steps,
+                     "peak_source": "measured vabsdiff4.add microbenchmark (profiles/sad_peak.md)",
+                     "hbm_peak_gbs": peaks.get("hbm_gbs")},
+        "clocks": clk.summary(),
+    }
+    if hres["cuts"] != res["cuts"] or hres["dissolves"] != res["dissolves"]:
+        line["warning"] = "host and device paths disagree"
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(spec)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--ref-frames", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--window", type=int, default=256, help="frames resident per clip")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

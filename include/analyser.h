@@ -90,6 +90,7 @@ typedef struct {
   int want_motion;                     /* keep level-0 motion fields of frame pairs (t,t+1) (0) */
   int tile_x, tile_y;                  /* pair-kernel tile in blocks (8x4, 4x4, 8x2, 16x2, 4x8);
                                           0 = autotuned per resolution (0, 0) */
+  int time_kernels;                    /* record CUDA events around every kernel launch (0) */
 } analyser_params;
 
 /* One measure of one pair, in the order of (kind, a, b). */
@@ -168,6 +169,17 @@ int analyser_last_error(const analyser* a, const char** message);
 /* Counters of the last run: pair measures computed, GPU waves, kernel launches. */
 int analyser_stats(const analyser* a, long long* pairs, long long* waves, long long* launches);
 
+/* Work and time counters (kernel times need params.time_kernels = 1). */
+typedef struct {
+  long long pairs, waves, launches;
+  long long pair_launches, pyramid_launches;
+  double pair_kernel_ms, pyramid_kernel_ms;  /* CUDA-event time on the library's stream */
+  double absdiff_ops;                        /* algorithmic |a-b| accumulates of the block search */
+  double pyramid_bytes;                      /* algorithmic bytes of the pyramid kernel (read + write) */
+  long long h2d_bytes, d2h_bytes;            /* host<->device bytes moved by the library */
+} analyser_profile_t;
+int analyser_profile(const analyser* a, analyser_profile_t* out);
+
 void analyser_destroy(analyser* a);
 
 /*
@@ -223,6 +235,9 @@ int server_step(server* s, int* active);
 
 /* Run server_step until every submitted clip is done. */
 int server_drain(server* s);
+
+/* Work and time counters of the server's engine. */
+int server_profile(const server* s, analyser_profile_t* out);
 
 /* Per-request timing: seconds from submit to results ready. */
 int server_latency(const server* s, long long ticket, double* seconds);

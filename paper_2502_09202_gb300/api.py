@@ -95,6 +95,11 @@ class Analyser:
         N.lib.analyser_stats(self._h, ctypes.byref(p), ctypes.byref(w), ctypes.byref(l))
         return {"pairs": p.value, "waves": w.value, "launches": l.value}
 
+    def profile(self) -> dict:
+        pr = N.Profile()
+        N.lib.analyser_profile(self._h, ctypes.byref(pr))
+        return pr.as_dict()
+
     def close(self):
         if self._h:
             N.lib.analyser_destroy(self._h)
@@ -226,6 +231,11 @@ class Server:
         if code == N.PENDING:
             return None
         return results_to_dict(r)
+
+    def profile(self) -> dict:
+        pr = N.Profile()
+        N.lib.server_profile(self._h, ctypes.byref(pr))
+        return pr.as_dict()
 
     def latency(self, ticket: int) -> float:
         s = ctypes.c_double()

@@ -106,6 +106,7 @@ int analyser_default_params(analyser_params* p) {
   p->want_motion = 0;
   p->tile_x = 0;
   p->tile_y = 0;
+  p->time_kernels = 0;
   return ANALYSER_OK;
 }
 
@@ -226,6 +227,13 @@ int analyser_stats(const analyser* a, long long* pairs, long long* waves, long l
   if (pairs) *pairs = a->eng ? a->eng->n_pairs : 0;
   if (waves) *waves = a->eng ? a->eng->n_waves : 0;
   if (launches) *launches = a->eng ? a->eng->n_launches : 0;
+  return ANALYSER_OK;
+}
+
+int analyser_profile(const analyser* a, analyser_profile_t* out) {
+  if (!a || !out) return ANALYSER_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  if (a->eng) a->eng->profile(out);
   return ANALYSER_OK;
 }
 
@@ -423,6 +431,13 @@ int server_poll(server* s, long long ticket, analyser_results_t* out) {
   if (s->status) return s->status;
   if (!it->second.done) return ANALYSER_PENDING;
   *out = it->second.res.r;
+  return ANALYSER_OK;
+}
+
+int server_profile(const server* s, analyser_profile_t* out) {
+  if (!s || !out) return ANALYSER_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  if (s->eng) s->eng->profile(out);
   return ANALYSER_OK;
 }
 

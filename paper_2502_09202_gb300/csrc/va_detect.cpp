@@ -82,7 +82,9 @@ void Detector::reset(const analyser_params& p, int64_t nb) {
 int Detector::keep_from() const {
   int k = t_ - p_.kmax - 1;
   for (const Shot& sh : open_) {
-    if (sh.next_eligible < sh.eligible.size()) k = std::min(k, sh.eligible[sh.next_eligible]);
+    // only shots that still need votes keep their next eligible frame resident
+    if (sh.analysed.size() < (size_t)p_.samp_max_frames && sh.next_eligible < sh.eligible.size())
+      k = std::min(k, sh.eligible[sh.next_eligible]);
   }
   return std::max(k, 0);
 }

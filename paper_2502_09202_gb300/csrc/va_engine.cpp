@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cstring>
 #include <map>
+#include <mutex>
 
 namespace va {
 
@@ -115,7 +116,23 @@ Engine::~Engine() {
   if (d_rec) cudaFree(d_rec);
   if (h_rec) cudaFreeHost(h_rec);
   if (d_vec) cudaFree(d_vec);
+  for (cudaEvent_t& e : ev_)
+    if (e) cudaEventDestroy(e);
   if (stream) cudaStreamDestroy(stream);
+}
+
+void Engine::profile(analyser_profile_t* out) const {
+  out->pairs = n_pairs;
+  out->waves = n_waves;
+  out->launches = n_launches;
+  out->pair_launches = n_pair_launches;
+  out->pyramid_launches = n_pyr_launches;
+  out->pair_kernel_ms = pair_ms;
+  out->pyramid_kernel_ms = pyr_ms;
+  out->absdiff_ops = absdiff_ops;
+  out->pyramid_bytes = pyr_bytes;
+  out->h2d_bytes = h2d_bytes;
+  out->d2h_bytes = d2h_bytes;
 }
 
 int Engine::init(std::string& why) {
@@ -135,6 +152,7 @@ int Engine::init(std::string& why) {
   VA_CUDA_TRY(cudaMalloc(&d_status, sizeof(int)), why);
   VA_CUDA_TRY(cudaMemset(d_status, 0, sizeof(int)), why);
   VA_CUDA_TRY(cudaMallocHost(&h_status, sizeof(int)), why);
+  for (cudaEvent_t& ev : ev_) VA_CUDA_TRY(cudaEventCreate(&ev), why);
   return ANALYSER_OK;
 }
 
@@ -199,6 +217,7 @@ int Engine::upload_host(Clip* c, const uint8_t* frames, long long pitch, int nfr
     c->l0[s] = dst;
     c->l0_pitch[s] = g.fp[0];
   }
+  h2d_bytes += (long long)k * g.W * g.H;
   c->pushed += k;
   return k;
 }
@@ -216,7 +235,24 @@ int Engine::attach_device(Clip* c, const uint8_t* frames, long long pitch, long 
   return k;
 }
 
+// Tile choices are a property of the device and the size, shared by every
+// engine of the process.
+static std::mutex g_tune_mu;
+static std::map<std::vector<int>, std::pair<int, int>> g_tune;
+
 void Engine::choose_tile(int width, int height, int* tbx, int* tby) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const std::vector<int> gkey = {dev, width, height, p.levels, p.radius_coarse, p.radius_refine};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(gkey);
+    if (it != g_tune.end()) {
+      *tbx = it->second.first;
+      *tby = it->second.second;
+      return;
+    }
+  }
   for (size_t i = 0; i < tune_keys_.size(); i++)
     if (tune_keys_[i] == std::make_pair(width, height)) {
       *tbx = tune_vals_[i].first;
@@ -278,6 +314,10 @@ void Engine::choose_tile(int width, int height, int* tbx, int* tby) {
   }
   tune_keys_.push_back({width, height});
   tune_vals_.push_back({bx, by});
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[gkey] = {bx, by};
+  }
   *tbx = bx;
   *tby = by;
 }
@@ -415,11 +455,14 @@ int Engine::wave() {
   });
   size_t vec_total = 0;
   for (auto& w : wp_) {
-    const bool dump = w.clip->want_vec_ && key_kind(w.key) == kFrame;
+    const int kind = key_kind(w.key);
+    const bool aon = kind == kFrame && key_b(w.key) == key_a(w.key) + 1;
+    const bool dump = w.clip->want_vec_ && (w.clip->stateless_ || aon);
     if (dump) {
       const Geometry& g = w.clip->geo;
+      const int h0 = kind == kFrame ? g.H : g.H / 2;
       w.vec_off = vec_total + 1;
-      vec_total += (size_t)(g.W / g.B0) * (g.H / g.B0);
+      vec_total += (size_t)(g.W / g.B0) * (h0 / g.B0);
     }
   }
   if (vec_total > cap_vec) {
@@ -476,12 +519,18 @@ int Engine::wave() {
     e = cudaMemcpyAsync(d_djobs, h_djobs, sizeof(DownJob) * ndown, cudaMemcpyHostToDevice, stream);
     if (e) return fail(e, "cudaMemcpyAsync(pyramid jobs)");
   }
+  const bool timed = p.time_kernels != 0;
+  if (timed && ndown) cudaEventRecord(ev_[0], stream);
   for (int l = 1; l < kMaxLevels; l++) {
     if (!dcount[l]) continue;
     e = launch_downsample(d_djobs + dstart[l], dcount[l], dmaxh[l], dmaxw[l], stream);
     if (e) return fail(e, "downsample_kernel");
     n_launches++;
+    n_pyr_launches++;
+    for (const DownJob& j : down[l]) pyr_bytes += 2.0 * (j.src.h / 2) * (double)(2 * (j.src.w / 2)) * 1.25;
   }
+  if (timed && ndown) cudaEventRecord(ev_[1], stream);
+  if (timed && !groups.empty()) cudaEventRecord(ev_[2], stream);
   for (const Group& gr : groups) {
     PairBatch b;
     b.jobs = d_pjobs + gr.first;
@@ -499,7 +548,9 @@ int Engine::wave() {
     e = launch_pairs(b, gr.tbx, gr.tby, grid, stream);
     if (e) return fail(e, "pair_kernel");
     n_launches++;
+    n_pair_launches++;
   }
+  if (timed && !groups.empty()) cudaEventRecord(ev_[3], stream);
   if (npairs) {
     e = cudaMemcpyAsync(h_rec, d_rec, sizeof(unsigned long long) * kRecWords * npairs, cudaMemcpyDeviceToHost, stream);
     if (e) return fail(e, "cudaMemcpyAsync(records)");
@@ -514,6 +565,22 @@ int Engine::wave() {
   e = cudaStreamSynchronize(stream);
   if (e) return fail(e, "cudaStreamSynchronize(wave)");
   const int dev_status = *h_status;
+  h2d_bytes += (long long)(sizeof(PairJob) * npairs + sizeof(DownJob) * ndown);
+  d2h_bytes += (long long)(sizeof(unsigned long long) * kRecWords * npairs + sizeof(short2) * vec_total + sizeof(int));
+  if (timed) {
+    float ms = 0.f;
+    if (ndown && cudaEventElapsedTime(&ms, ev_[0], ev_[1]) == cudaSuccess) pyr_ms += ms;
+    if (!groups.empty() && cudaEventElapsedTime(&ms, ev_[2], ev_[3]) == cudaSuccess) pair_ms += ms;
+  }
+  // algorithmic block-search work: |a-b| accumulates per block over all levels
+  {
+    const int L = p.levels, B0 = kCoarseSide << (L - 1);
+    const double cw = (double)(2 * p.radius_coarse + 1) * (2 * p.radius_coarse + 1);
+    const double rw = (double)(2 * p.radius_refine + 1) * (2 * p.radius_refine + 1);
+    double per_block = kCoarseSide * kCoarseSide * cw;
+    for (int l = L - 2; l >= 0; l--) per_block += (double)(B0 >> l) * (B0 >> l) * rw;
+    for (int i = 0; i < npairs; i++) absdiff_ops += per_block * h_pjobs[i].nbx * h_pjobs[i].nby;
+  }
   if (dev_status) {
     status = ANALYSER_ERR_CUDA;
     message = "device-side check failed in pair_kernel (motion vector outside the AMM table)";
@@ -539,7 +606,7 @@ int Engine::wave() {
     c->inflight.erase(w.key);
     if (w.vec_off) {
       const int a = key_a(w.key);
-      const size_t nbk = (size_t)(g.W / g.B0) * (g.H / g.B0);
+      const size_t nbk = (size_t)(g.W / g.B0) * (h0 / g.B0);
       if (c->stateless_) {
         c->vec_out_.push_back({w.key, std::vector<short2>(h_vec.begin() + (w.vec_off - 1),
                                                          h_vec.begin() + (w.vec_off - 1) + nbk)});

@@ -115,6 +115,10 @@ class Engine {
   std::vector<Clip*> clips;
   cudaStream_t stream = nullptr;
   long long n_pairs = 0, n_waves = 0, n_launches = 0;
+  long long n_pair_launches = 0, n_pyr_launches = 0;
+  double pair_ms = 0.0, pyr_ms = 0.0, absdiff_ops = 0.0, pyr_bytes = 0.0;
+  long long h2d_bytes = 0, d2h_bytes = 0;
+  void profile(analyser_profile_t* out) const;
   int status = ANALYSER_OK;
   std::string message;
   bool autotune = true;
@@ -130,6 +134,7 @@ class Engine {
   int qmax = 0;
   int* d_status = nullptr;
   int* h_status = nullptr;
+  cudaEvent_t ev_[4] = {nullptr, nullptr, nullptr, nullptr};
   int sm_count = 0;
   // wave buffers
   int cap_pairs = 0, cap_down = 0;

@@ -31,7 +31,7 @@ class Params(ctypes.Structure):
         ("pulldown_match", c_double),
         ("kf_theta", c_double),
         ("device", c_int), ("window_frames", c_int), ("mem_budget_bytes", c_ull), ("want_motion", c_int),
-        ("tile_x", c_int), ("tile_y", c_int),
+        ("tile_x", c_int), ("tile_y", c_int), ("time_kernels", c_int),
     ]
 
 
@@ -58,6 +58,15 @@ class Results(ctypes.Structure):
                 ("motion_w", c_int), ("motion_h", c_int), ("motion", ctypes.POINTER(ctypes.c_int16))]
 
 
+class Profile(ctypes.Structure):
+    _fields_ = [("pairs", c_ll), ("waves", c_ll), ("launches", c_ll), ("pair_launches", c_ll),
+                ("pyramid_launches", c_ll), ("pair_kernel_ms", c_double), ("pyramid_kernel_ms", c_double),
+                ("absdiff_ops", c_double), ("pyramid_bytes", c_double), ("h2d_bytes", c_ll), ("d2h_bytes", c_ll)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 MEASURE_FN = ctypes.CFUNCTYPE(c_int, ctypes.c_void_p, c_int, c_int, c_int, ctypes.POINTER(c_i64))
 
 # every entry point of include/analyser.h: name -> (restype, argtypes)
@@ -71,6 +80,7 @@ SIGNATURES = {
     "analyser_results": (c_int, [VP, P(Results)]),
     "analyser_last_error": (c_int, [VP, P(ctypes.c_char_p)]),
     "analyser_stats": (c_int, [VP, P(c_ll), P(c_ll), P(c_ll)]),
+    "analyser_profile": (c_int, [VP, P(Profile)]),
     "analyser_destroy": (None, [VP]),
     "analyser_measure_pairs": (c_int, [P(Params), c_int, c_int, VP, c_ll, c_ll, c_int, P(c_int), P(c_int),
                                        P(c_int), c_int, P(c_i64), P(ctypes.c_int16), VP]),
@@ -80,6 +90,7 @@ SIGNATURES = {
     "server_step": (c_int, [VP, P(c_int)]),
     "server_drain": (c_int, [VP]),
     "server_poll": (c_int, [VP, c_ll, P(Results)]),
+    "server_profile": (c_int, [VP, P(Profile)]),
     "server_latency": (c_int, [VP, c_ll, P(c_double)]),
     "server_release": (c_int, [VP, c_ll]),
     "server_destroy": (None, [VP]),

@@ -197,3 +197,20 @@ def test_full_size_1080p_sampled_pairs():
         ref, vec = _oracle_pair(kinds[k], frames[ia[k]], frames[ib[k]])
         assert list(rec[k]) == [ref[f] for f in REC7]
         assert np.array_equal(mot[k], vec)
+
+
+def test_long_clip_streams_through_a_small_window():
+    """A clip several windows long, pushed in uneven chunks: the window must keep
+    advancing and the results must not depend on the chunking."""
+    api = _api()
+    spec = synth.config_interlaced(nframes=260, width=256, height=144)
+    frames = synth.Clip(spec).frames()
+    ref = OA.analyse_frames(frames)
+    for chunks in ((260,), (7, 100, 1, 152)):
+        with api.Analyser(spec.width, spec.height, spec.fps, window_frames=24) as a:
+            s = 0
+            for c in chunks:
+                a.push(frames[s:s + c])
+                s += c
+            a.finish()
+            _compare_results(a.results(), ref)
