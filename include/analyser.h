@@ -208,6 +208,14 @@ typedef int (*analyser_measure_fn)(void* ctx, int kind, int a, int b, int64_t* r
 int analyser_detect_offline(const analyser_params* p, int width, int height, int nframes,
                             analyser_measure_fn get, void* ctx, analyser** out);
 
+/*
+ * Throughput of the packed-byte SAD instruction the search kernels issue
+ * (vabsdiff4 with accumulate) in a register-only loop over every SM, in
+ * 10^12 |a-b| accumulates per second: the peak against which the pair
+ * kernel's roofline fraction is reported.  Needs a GPU; runs ~50 ms.
+ */
+int analyser_measure_sad_peak(int device, double* tera_per_s);
+
 /* ---- serving: continuous batching of many clips on one GPU ------------------- */
 
 /* A server admits clips while the device-memory budget allows. */

@@ -13,7 +13,7 @@ from . import native as N
 from .native import AnalyserError, default_params
 
 __all__ = ["Analyser", "Server", "measure_pairs", "detect_offline", "default_params", "AnalyserError",
-           "results_to_dict"]
+           "results_to_dict", "sad_peak"]
 
 
 def _check(code: int, where: str, handle=None):
@@ -166,6 +166,13 @@ def measure_pairs(frames, kinds, ia, ib, params: N.Params | None = None, want_mo
             off += m
         return rec, out
     return rec, None
+
+
+def sad_peak(device: int = 0) -> float:
+    """Measured packed-SAD throughput of this GPU, 10^12 |a-b| accumulates per second."""
+    v = ctypes.c_double()
+    _check(N.lib.analyser_measure_sad_peak(device, ctypes.byref(v)), "analyser_measure_sad_peak")
+    return v.value
 
 
 def detect_offline(width: int, height: int, nframes: int, get_record, params: N.Params | None = None,
