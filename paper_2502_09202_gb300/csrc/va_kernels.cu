@@ -96,6 +96,87 @@ cudaError_t launch_downsample(const DownJob* d_jobs, int njobs, int max_dst_h, i
 // fused pair kernel
 // ---------------------------------------------------------------------------
 
+// Refinement of every block of a tile at one pyramid level (block side S,
+// radius RR), candidates v = 2*parent + d, |d| <= RR.  Each block's
+// (S+2RR)-row search window is staged in shared memory; a thread owns one
+// (block, dx, 4-pixel column) with that I column in registers and slides down
+// the window rows, feeding the 2RR+1 dy candidates; the NQ column partials
+// are then summed with shuffles.
+template <int S, int RR, int NT, int NB, int TBX>
+__device__ __forceinline__ void refine_level(const Plane Il, const Plane Jl, int bx0, int by0, int nbx, int nby,
+                                             int lam, const int* s_vx, const int* s_vy,
+                                             unsigned long long* s_best64, uint32_t* s_win, int tid) {
+  constexpr int NQ = S / 4, ND = 2 * RR + 1, PER = ND * NQ;
+  constexpr int WR = S + 2 * RR, WW = (S + 2 * RR + 2) / 4 + 1;
+  for (int idx = tid; idx < NB * WR * WW; idx += NT) {
+    const int bl = idx / (WR * WW), rem = idx - bl * (WR * WW);
+    const int w = rem / WW, k = rem - w * WW;
+    const int bx = bx0 + bl % TBX, by = by0 + bl / TBX;
+    uint32_t v = 0;
+    if (bx < nbx && by < nby) {
+      const int xstart = bx * S + 2 * s_vx[bl] - RR;
+      const int xs = xstart & ~3;
+      const int yy = clampi(by * S + 2 * s_vy[bl] - RR + w, 0, Jl.h - 1);
+      const int xx = xs + 4 * k;
+      const uint8_t* row = Jl.p + (size_t)yy * Jl.pitch;
+      v = (xx >= 0 && xx + 3 <= Jl.w - 1) ? __ldg(reinterpret_cast<const uint32_t*>(row + xx))
+                                          : load4_clamped(row, xx, Jl.w);
+    }
+    s_win[idx] = v;
+  }
+  __syncthreads();
+  for (int base = 0; base < NB * PER; base += NT) {
+    const int it = base + tid;
+    const int bl = it / PER, rem = it - bl * PER;
+    const int dxi = rem / NQ, q = rem - dxi * NQ;
+    const int bx = bx0 + bl % TBX, by = by0 + bl / TBX;
+    const bool valid = it < NB * PER && bx < nbx && by < nby;
+    uint32_t acc[ND];
+#pragma unroll
+    for (int d = 0; d < ND; d++) acc[d] = 0;
+    int cx = 0, cy = 0;
+    if (valid) {
+      cx = 2 * s_vx[bl];
+      cy = 2 * s_vy[bl];
+      uint32_t icol[S];
+      const uint8_t* ip = Il.p + (size_t)(by * S) * Il.pitch + bx * S + 4 * q;
+#pragma unroll
+      for (int i = 0; i < S; i++) icol[i] = __ldg(reinterpret_cast<const uint32_t*>(ip + (size_t)i * Il.pitch));
+      const int xstart = bx * S + cx - RR;
+      const int o = (xstart - (xstart & ~3)) + dxi + 4 * q;
+      const int wo = o >> 2, sh = (o & 3) * 8;
+      const uint32_t* wp = s_win + bl * (WR * WW) + wo;
+#pragma unroll
+      for (int w = 0; w < WR; w++) {
+        const uint32_t jw = __funnelshift_r(wp[w * WW], wp[w * WW + 1], sh);
+#pragma unroll
+        for (int d = 0; d < ND; d++) {
+          const int i = w - d;
+          if (i >= 0 && i < S) acc[d] = sad4(icol[i], jw, acc[d]);
+        }
+      }
+    }
+#pragma unroll
+    for (int off = NQ / 2; off >= 1; off >>= 1) {
+#pragma unroll
+      for (int d = 0; d < ND; d++) acc[d] += __shfl_xor_sync(0xFFFFFFFFu, acc[d], off);
+    }
+    if (valid && q == 0) {
+      unsigned long long best = ~0ull;
+#pragma unroll
+      for (int d = 0; d < ND; d++) {
+        const int vx = cx + dxi - RR, vy = cy + d - RR;
+        const int n1 = abs(vx) + abs(vy);
+        const unsigned long long key = ((unsigned long long)(acc[d] + (uint32_t)(lam * n1)) << 32) |
+                                       ((unsigned long long)n1 << 20) | ((unsigned long long)(vy + 512) << 10) |
+                                       (unsigned long long)(vx + 512);
+        best = key < best ? key : best;
+      }
+      atomicMin(&s_best64[bl], best);
+    }
+  }
+}
+
 template <int R, int TBX, int TBY>
 struct PairShape {
   static constexpr int G = (2 * R + 4) / 4;       // vx groups of 4 candidates
@@ -121,6 +202,8 @@ pair_kernel(const PairBatch b) {
   __shared__ int s_vx[NB], s_vy[NB];
   __shared__ unsigned long long s_red[S::NW][kRecWords];
   __shared__ PairJob s_job;
+  // refinement windows: level side 16 with radius 2 is the largest fast case
+  __shared__ uint32_t s_win[NB * 20 * 6];
 
   const int tid = threadIdx.x;
   const int L = b.cfg.levels;
@@ -180,6 +263,8 @@ pair_kernel(const PairBatch b) {
       const uint32_t i0 = s_iw[byl * 4 + 0][bxl], i1 = s_iw[byl * 4 + 1][bxl];
       const uint32_t i2 = s_iw[byl * 4 + 2][bxl], i3 = s_iw[byl * 4 + 3][bxl];
       const uint32_t lam18 = (uint32_t)lam << 18;
+      // acc[j][c & 3] holds candidate c = dy - k (vy = c - R): it receives row k
+      // of the block at window row dy, starts at k = 0 and completes at k = 3.
       uint32_t acc[4][4];
       uint32_t best[4];
 #pragma unroll
@@ -199,24 +284,17 @@ pair_kernel(const PairBatch b) {
         w[3] = __funnelshift_r(wlo, whi, 24);
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-          acc[j][0] = sad4(i0, w[j], acc[j][0]);
-          acc[j][1] = sad4(i1, w[j], acc[j][1]);
-          acc[j][2] = sad4(i2, w[j], acc[j][2]);
-          acc[j][3] = sad4(i3, w[j], acc[j][3]);
+          if (dy <= 2 * R) acc[j][dy & 3] = sad4(i0, w[j], 0u);
+          if (dy >= 1 && dy - 1 <= 2 * R) acc[j][(dy - 1) & 3] = sad4(i1, w[j], acc[j][(dy - 1) & 3]);
+          if (dy >= 2 && dy - 2 <= 2 * R) acc[j][(dy - 2) & 3] = sad4(i2, w[j], acc[j][(dy - 2) & 3]);
+          if (dy >= 3) acc[j][(dy - 3) & 3] = sad4(i3, w[j], acc[j][(dy - 3) & 3]);
         }
         if (dy >= 3) {
           const int vy = dy - R - 3;
           const int avy = vy < 0 ? -vy : vy;
           const uint32_t bv = lam18 * (uint32_t)avy + (((uint32_t)avy << 12) | ((uint32_t)(vy + R) << 6));
 #pragma unroll
-          for (int j = 0; j < 4; j++) best[j] = min(best[j], (acc[j][3] << 18) + bv);
-        }
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-          acc[j][3] = acc[j][2];
-          acc[j][2] = acc[j][1];
-          acc[j][1] = acc[j][0];
-          acc[j][0] = 0;
+          for (int j = 0; j < 4; j++) best[j] = min(best[j], (acc[j][(dy - 3) & 3] << 18) + bv);
         }
       }
       uint32_t tbest = 0xFFFFFFFFu;
@@ -246,32 +324,38 @@ pair_kernel(const PairBatch b) {
       const int lim_w = min(Jl.w, Jl.pitch);
       for (int i = tid; i < NB; i += NT) s_best64[i] = ~0ull;
       __syncthreads();
-      for (int t = tid; t < NB * ncand; t += NT) {
-        const int bl = t / ncand, c = t - bl * ncand;
-        const int bxl = bl % TBX, byl = bl / TBX;
-        const int bx = bx0 + bxl, by = by0 + byl;
-        if (bx >= nbx || by >= nby) continue;
-        const int vx = 2 * s_vx[bl] + (c % side) - rr;
-        const int vy = 2 * s_vy[bl] + (c / side) - rr;
-        const int x0 = bx * s, y0 = by * s;
-        const int xj = x0 + vx;
-        const bool fast = (xj >= 0) && (xj + s + 3 <= lim_w - 1) && (y0 + vy >= 0) && (y0 + vy + s - 1 <= Jl.h - 1);
-        uint32_t sad = 0;
-        for (int y = 0; y < s; y++) {
-          const uint8_t* irow = Il.p + (size_t)(y0 + y) * Il.pitch + x0;
-          const int yj = clampi(y0 + y + vy, 0, Jl.h - 1);
-          const uint8_t* jrow = Jl.p + (size_t)yj * Jl.pitch;
-          for (int x = 0; x < s; x += 4) {
-            const uint32_t iv = __ldg(reinterpret_cast<const uint32_t*>(irow + x));
-            const uint32_t jv = fast ? load4_unaligned(jrow, xj + x) : load4_clamped(jrow, xj + x, Jl.w);
-            sad = sad4(iv, jv, sad);
+      if (rr == 2 && s == 16) {
+        refine_level<16, 2, NT, NB, TBX>(Il, Jl, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_best64, s_win, tid);
+      } else if (rr == 2 && s == 8) {
+        refine_level<8, 2, NT, NB, TBX>(Il, Jl, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_best64, s_win, tid);
+      } else {
+        for (int t = tid; t < NB * ncand; t += NT) {
+          const int bl = t / ncand, c = t - bl * ncand;
+          const int bxl = bl % TBX, byl = bl / TBX;
+          const int bx = bx0 + bxl, by = by0 + byl;
+          if (bx >= nbx || by >= nby) continue;
+          const int vx = 2 * s_vx[bl] + (c % side) - rr;
+          const int vy = 2 * s_vy[bl] + (c / side) - rr;
+          const int x0 = bx * s, y0 = by * s;
+          const int xj = x0 + vx;
+          const bool fast = (xj >= 0) && (xj + s + 3 <= lim_w - 1) && (y0 + vy >= 0) && (y0 + vy + s - 1 <= Jl.h - 1);
+          uint32_t sad = 0;
+          for (int y = 0; y < s; y++) {
+            const uint8_t* irow = Il.p + (size_t)(y0 + y) * Il.pitch + x0;
+            const int yj = clampi(y0 + y + vy, 0, Jl.h - 1);
+            const uint8_t* jrow = Jl.p + (size_t)yj * Jl.pitch;
+            for (int x = 0; x < s; x += 4) {
+              const uint32_t iv = __ldg(reinterpret_cast<const uint32_t*>(irow + x));
+              const uint32_t jv = fast ? load4_unaligned(jrow, xj + x) : load4_clamped(jrow, xj + x, Jl.w);
+              sad = sad4(iv, jv, sad);
+            }
           }
+          const int n1 = abs(vx) + abs(vy);
+          const unsigned long long key = ((unsigned long long)(sad + (uint32_t)(lam * n1)) << 32) |
+                                         ((unsigned long long)n1 << 20) | ((unsigned long long)(vy + 512) << 10) |
+                                         (unsigned long long)(vx + 512);
+          atomicMin(&s_best64[bl], key);
         }
-        const int n1 = abs(vx) + abs(vy);
-        const unsigned long long key = ((unsigned long long)(sad + (uint32_t)(lam * n1)) << 32) |
-                                       ((unsigned long long)n1 << 20) | ((unsigned long long)(vy + 512) << 10) |
-                                       (unsigned long long)(vx + 512);
-        atomicMin(&s_best64[bl], key);
       }
       __syncthreads();
       for (int i = tid; i < NB; i += NT) {
