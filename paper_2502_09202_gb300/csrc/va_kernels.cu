@@ -96,85 +96,142 @@ cudaError_t launch_downsample(const DownJob* d_jobs, int njobs, int max_dst_h, i
 // fused pair kernel
 // ---------------------------------------------------------------------------
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Refinement of every block of a tile at one pyramid level (block side S,
-// radius RR), candidates v = 2*parent + d, |d| <= RR.  Each block's
-// (S+2RR)-row search window is staged in shared memory; a thread owns one
-// (block, dx, 4-pixel column) with that I column in registers and slides down
-// the window rows, feeding the 2RR+1 dy candidates; the NQ column partials
-// are then summed with shuffles.
+// radius RR), candidates v = 2*parent + d, |d| <= RR.
+//  - each block's (S+2RR)-row search window in J is staged in shared memory
+//    (clamp-to-edge);
+//  - a thread owns one (block, dx, 4-pixel column q) with that I column in
+//    registers (read from the tile staged in s_i) and slides down the window
+//    rows, feeding the 2RR+1 dy candidates; the S/4 column partials are summed
+//    with xor shuffles;
+//  - a candidate's key is (cost << 8) | t with cost = SAD + lambda*|v|_1 and
+//    t = (|v|_1 - min|v|_1)*25 + dy_i*5 + dx_i, which orders the block's 25
+//    candidates exactly as (cost, |v|_1, vy, vx); the minimum goes to s_best.
+// Afterwards s_vx/s_vy hold the level-l vectors.
 template <int S, int RR, int NT, int NB, int TBX>
-__device__ __forceinline__ void refine_level(const Plane Il, const Plane Jl, int bx0, int by0, int nbx, int nby,
-                                             int lam, const int* s_vx, const int* s_vy,
-                                             unsigned long long* s_best64, uint32_t* s_win, int tid) {
-  constexpr int NQ = S / 4, ND = 2 * RR + 1, PER = ND * NQ;
+__device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i, int bx0, int by0, int nbx, int nby,
+                                             int lam, int* s_vx, int* s_vy, uint32_t* s_best, uint32_t* s_win,
+                                             int tid) {
+  static_assert(RR == 2, "relative candidate ranks assume radius 2");
+  constexpr int NQ = S / 4, ND = 2 * RR + 1;
   constexpr int WR = S + 2 * RR, WW = (S + 2 * RR + 2) / 4 + 1;
-  for (int idx = tid; idx < NB * WR * WW; idx += NT) {
-    const int bl = idx / (WR * WW), rem = idx - bl * (WR * WW);
-    const int w = rem / WW, k = rem - w * WW;
+  constexpr int IW = TBX * NQ;     // words per row of the staged I tile
+  for (int task = tid; task < NB * WR; task += NT) {
+    const int bl = task / WR, w = task - bl * WR;
     const int bx = bx0 + bl % TBX, by = by0 + bl / TBX;
-    uint32_t v = 0;
+    uint32_t* dst = s_win + task * WW;
     if (bx < nbx && by < nby) {
-      const int xstart = bx * S + 2 * s_vx[bl] - RR;
-      const int xs = xstart & ~3;
+      const int xs = (bx * S + 2 * s_vx[bl] - RR) & ~3;
       const int yy = clampi(by * S + 2 * s_vy[bl] - RR + w, 0, Jl.h - 1);
-      const int xx = xs + 4 * k;
       const uint8_t* row = Jl.p + (size_t)yy * Jl.pitch;
-      v = (xx >= 0 && xx + 3 <= Jl.w - 1) ? __ldg(reinterpret_cast<const uint32_t*>(row + xx))
-                                          : load4_clamped(row, xx, Jl.w);
-    }
-    s_win[idx] = v;
-  }
-  __syncthreads();
-  for (int base = 0; base < NB * PER; base += NT) {
-    const int it = base + tid;
-    const int bl = it / PER, rem = it - bl * PER;
-    const int dxi = rem / NQ, q = rem - dxi * NQ;
-    const int bx = bx0 + bl % TBX, by = by0 + bl / TBX;
-    const bool valid = it < NB * PER && bx < nbx && by < nby;
-    uint32_t acc[ND];
+      if (xs >= 0 && xs + 4 * WW <= Jl.w) {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(row + xs);
 #pragma unroll
-    for (int d = 0; d < ND; d++) acc[d] = 0;
+        for (int k = 0; k < WW; k++) dst[k] = __ldg(src + k);
+      } else {
+#pragma unroll
+        for (int k = 0; k < WW; k++) dst[k] = load4_clamped(row, xs + 4 * k, Jl.w);
+      }
+    }
+  }
+  for (int i = tid; i < NB; i += NT) s_best[i] = 0xFFFFFFFFu;
+  __syncthreads();
+  // task = (block, 4-pixel column q): all ND x ND candidates of that column
+  for (int base = 0; base < NB * NQ; base += NT) {
+    const int it = base + tid;
+    const int bl = it / NQ, q = it - bl * NQ;
+    const int bxl = bl % TBX, byl = bl / TBX;
+    const bool valid = it < NB * NQ && bx0 + bxl < nbx && by0 + byl < nby;
+    uint32_t acc[ND][ND];     // [dx][dy]
+#pragma unroll
+    for (int a = 0; a < ND; a++)
+#pragma unroll
+      for (int d = 0; d < ND; d++) acc[a][d] = 0;
     int cx = 0, cy = 0;
     if (valid) {
       cx = 2 * s_vx[bl];
       cy = 2 * s_vy[bl];
       uint32_t icol[S];
-      const uint8_t* ip = Il.p + (size_t)(by * S) * Il.pitch + bx * S + 4 * q;
+      const uint32_t* ip = s_i + (byl * S) * IW + bxl * NQ + q;
 #pragma unroll
-      for (int i = 0; i < S; i++) icol[i] = __ldg(reinterpret_cast<const uint32_t*>(ip + (size_t)i * Il.pitch));
-      const int xstart = bx * S + cx - RR;
-      const int o = (xstart - (xstart & ~3)) + dxi + 4 * q;
+      for (int i = 0; i < S; i++) icol[i] = ip[i * IW];
+      const int xstart = (bx0 + bxl) * S + cx - RR;
+      const int o = (xstart - (xstart & ~3)) + 4 * q;    // byte offset of dx = 0 in the window row
       const int wo = o >> 2, sh = (o & 3) * 8;
       const uint32_t* wp = s_win + bl * (WR * WW) + wo;
 #pragma unroll
       for (int w = 0; w < WR; w++) {
-        const uint32_t jw = __funnelshift_r(wp[w * WW], wp[w * WW + 1], sh);
+        const uint32_t w0 = wp[w * WW], w1 = wp[w * WW + 1], w2 = wp[w * WW + 2];
+        // the 5 dx alignments come from 3 consecutive words
+        const uint64_t lo = ((uint64_t)w1 << 32) | w0;
+        const uint64_t hi = ((uint64_t)w2 << 32) | w1;
+        uint32_t jw[ND];
+#pragma unroll
+        for (int a = 0; a < ND; a++) {
+          // byte offset o&3 + a within w0..w2
+          const int bo = a;   // added to the runtime shift below
+          jw[a] = (sh + 8 * bo < 32) ? (uint32_t)(lo >> (sh + 8 * bo)) : (uint32_t)(hi >> (sh + 8 * bo - 32));
+        }
 #pragma unroll
         for (int d = 0; d < ND; d++) {
           const int i = w - d;
-          if (i >= 0 && i < S) acc[d] = sad4(icol[i], jw, acc[d]);
+          if (i >= 0 && i < S) {
+#pragma unroll
+            for (int a = 0; a < ND; a++) acc[a][d] = sad4(icol[i], jw[a], acc[a][d]);
+          }
         }
       }
     }
 #pragma unroll
     for (int off = NQ / 2; off >= 1; off >>= 1) {
 #pragma unroll
-      for (int d = 0; d < ND; d++) acc[d] += __shfl_xor_sync(0xFFFFFFFFu, acc[d], off);
+      for (int a = 0; a < ND; a++)
+#pragma unroll
+        for (int d = 0; d < ND; d++) acc[a][d] += __shfl_xor_sync(0xFFFFFFFFu, acc[a][d], off);
     }
-    if (valid && q == 0) {
-      unsigned long long best = ~0ull;
+    // every column lane holds all sums: lane q finalises the dy rows d = q (mod NQ)
+    uint32_t best = 0xFFFFFFFFu;
+    if (valid) {
+      const int n1min = max(abs(cx) - RR, 0) + max(abs(cy) - RR, 0);
 #pragma unroll
       for (int d = 0; d < ND; d++) {
-        const int vx = cx + dxi - RR, vy = cy + d - RR;
-        const int n1 = abs(vx) + abs(vy);
-        const unsigned long long key = ((unsigned long long)(acc[d] + (uint32_t)(lam * n1)) << 32) |
-                                       ((unsigned long long)n1 << 20) | ((unsigned long long)(vy + 512) << 10) |
-                                       (unsigned long long)(vx + 512);
-        best = key < best ? key : best;
+        if (d % NQ == q) {
+          const int avy = abs(cy + d - RR);
+#pragma unroll
+          for (int a = 0; a < ND; a++) {
+            const int n1 = abs(cx + a - RR) + avy;
+            const uint32_t cost = acc[a][d] + (uint32_t)(lam * n1);
+            const uint32_t t = (uint32_t)((n1 - n1min) * 25 + d * 5 + a);
+            best = min(best, (cost << 8) | t);
+          }
+        }
       }
-      atomicMin(&s_best64[bl], best);
+    }
+#pragma unroll
+    for (int off = NQ / 2; off >= 1; off >>= 1) best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, off));
+    if (valid && q == 0) atomicMin(&s_best[bl], best);
+  }
+  __syncthreads();
+  for (int i = tid; i < NB; i += NT) {
+    const uint32_t k = s_best[i];
+    if (k != 0xFFFFFFFFu) {
+      const int t = (int)(k & 255u) % 25;
+      s_vx[i] = 2 * s_vx[i] + (t % 5) - RR;
+      s_vy[i] = 2 * s_vy[i] + (t / 5) - RR;
     }
   }
+  __syncthreads();
 }
 
 template <int R, int TBX, int TBY>
@@ -182,14 +239,17 @@ struct PairShape {
   static constexpr int G = (2 * R + 4) / 4;       // vx groups of 4 candidates
   static constexpr int NB = TBX * TBY;            // blocks per tile
   static constexpr int NA = NB * G;               // threads busy in the coarse phase
-  static constexpr int NT = (NA + 31) / 32 * 32;  // threads (whole warps)
+  // whole warps, and at least 10 per 32 blocks so that the refinement tasks
+  // (blocks x 5 dx x 4 columns at level 0, x 2 columns at level 1) fill 2 and 1 rounds
+  static constexpr int NT0 = (NA + 31) / 32 * 32;
+  static constexpr int NT = NT0 > NB * 10 ? NT0 : NB * 10;
   static constexpr int WROWS = TBY * kCoarseSide + 2 * R;
   static constexpr int WWORDS = TBX + G;
   static constexpr int NW = (NT + 31) / 32;
 };
 
 template <int R, int TBX, int TBY>
-__global__ void __launch_bounds__(PairShape<R, TBX, TBY>::NT)
+__global__ void __launch_bounds__(PairShape<R, TBX, TBY>::NT, 3)
 pair_kernel(const PairBatch b) {
   using S = PairShape<R, TBX, TBY>;
   constexpr int G = S::G, NB = S::NB, NT = S::NT, WROWS = S::WROWS, WWORDS = S::WWORDS;
@@ -204,6 +264,9 @@ pair_kernel(const PairBatch b) {
   __shared__ PairJob s_job;
   // refinement windows: level side 16 with radius 2 is the largest fast case
   __shared__ uint32_t s_win[NB * 20 * 6];
+  // I tiles of levels 0 and 1 (fast path: 3 levels, radius 2), staged asynchronously
+  __shared__ __align__(16) uint32_t s_i0[TBY * 16 * TBX * 4];
+  __shared__ __align__(16) uint32_t s_i1[TBY * 8 * TBX * 2];
 
   const int tid = threadIdx.x;
   const int L = b.cfg.levels;
@@ -230,6 +293,22 @@ pair_kernel(const PairBatch b) {
     const int local = item - jb.item_begin;
     const int bx0 = (local % jb.tiles_x) * TBX, by0 = (local / jb.tiles_x) * TBY;
     const int nbx = jb.nbx, nby = jb.nby;
+    const bool fast = (L == 3 && rr == 2);
+    if (fast) {
+      // I tiles of levels 0 and 1 for the refinement and the correlation sums:
+      // copied while the coarse search runs
+      for (int c = tid; c < TBY * 16 * TBX; c += NT) {
+        const int r = c / TBX, k = c - r * TBX;
+        if (bx0 + k < nbx && by0 + r / 16 < nby)
+          cp_async16(s_i0 + (r * TBX + k) * 4, jb.I[0].p + (size_t)(by0 * 16 + r) * jb.I[0].pitch + (bx0 + k) * 16);
+      }
+      for (int c = tid; c < TBY * 8 * TBX; c += NT) {
+        const int r = c / TBX, k = c - r * TBX;
+        if (bx0 + k < nbx && by0 + r / 8 < nby)
+          cp_async8(s_i1 + (r * TBX + k) * 2, jb.I[1].p + (size_t)(by0 * 8 + r) * jb.I[1].pitch + (bx0 + k) * 8);
+      }
+      cp_async_commit();
+    }
 
     // ---- phase A: exhaustive search on the coarsest level --------------------
     {
@@ -318,17 +397,18 @@ pair_kernel(const PairBatch b) {
     }
 
     // ---- phase B: refinement at levels L-2 .. 0 -------------------------------
-    for (int l = L - 2; l >= 0; l--) {
-      const Plane Il = jb.I[l], Jl = jb.J[l];
-      const int s = B0 >> l;
-      const int lim_w = min(Jl.w, Jl.pitch);
-      for (int i = tid; i < NB; i += NT) s_best64[i] = ~0ull;
+    if (fast) {
+      cp_async_wait_all();
       __syncthreads();
-      if (rr == 2 && s == 16) {
-        refine_level<16, 2, NT, NB, TBX>(Il, Jl, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_best64, s_win, tid);
-      } else if (rr == 2 && s == 8) {
-        refine_level<8, 2, NT, NB, TBX>(Il, Jl, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_best64, s_win, tid);
-      } else {
+      refine_level<8, 2, NT, NB, TBX>(jb.J[1], s_i1, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_best32, s_win, tid);
+      refine_level<16, 2, NT, NB, TBX>(jb.J[0], s_i0, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_best32, s_win, tid);
+    } else {
+      for (int l = L - 2; l >= 0; l--) {
+        const Plane Il = jb.I[l], Jl = jb.J[l];
+        const int s = B0 >> l;
+        const int lim_w = min(Jl.w, Jl.pitch);
+        for (int i = tid; i < NB; i += NT) s_best64[i] = ~0ull;
+        __syncthreads();
         for (int t = tid; t < NB * ncand; t += NT) {
           const int bl = t / ncand, c = t - bl * ncand;
           const int bxl = bl % TBX, byl = bl / TBX;
@@ -338,7 +418,7 @@ pair_kernel(const PairBatch b) {
           const int vy = 2 * s_vy[bl] + (c / side) - rr;
           const int x0 = bx * s, y0 = by * s;
           const int xj = x0 + vx;
-          const bool fast = (xj >= 0) && (xj + s + 3 <= lim_w - 1) && (y0 + vy >= 0) && (y0 + vy + s - 1 <= Jl.h - 1);
+          const bool fastj = (xj >= 0) && (xj + s + 3 <= lim_w - 1) && (y0 + vy >= 0) && (y0 + vy + s - 1 <= Jl.h - 1);
           uint32_t sad = 0;
           for (int y = 0; y < s; y++) {
             const uint8_t* irow = Il.p + (size_t)(y0 + y) * Il.pitch + x0;
@@ -346,7 +426,7 @@ pair_kernel(const PairBatch b) {
             const uint8_t* jrow = Jl.p + (size_t)yj * Jl.pitch;
             for (int x = 0; x < s; x += 4) {
               const uint32_t iv = __ldg(reinterpret_cast<const uint32_t*>(irow + x));
-              const uint32_t jv = fast ? load4_unaligned(jrow, xj + x) : load4_clamped(jrow, xj + x, Jl.w);
+              const uint32_t jv = fastj ? load4_unaligned(jrow, xj + x) : load4_clamped(jrow, xj + x, Jl.w);
               sad = sad4(iv, jv, sad);
             }
           }
@@ -356,16 +436,16 @@ pair_kernel(const PairBatch b) {
                                          (unsigned long long)(vx + 512);
           atomicMin(&s_best64[bl], key);
         }
-      }
-      __syncthreads();
-      for (int i = tid; i < NB; i += NT) {
-        const unsigned long long k = s_best64[i];
-        if (k != ~0ull) {
-          s_vx[i] = (int)(k & 1023ull) - 512;
-          s_vy[i] = (int)((k >> 10) & 1023ull) - 512;
+        __syncthreads();
+        for (int i = tid; i < NB; i += NT) {
+          const unsigned long long k = s_best64[i];
+          if (k != ~0ull) {
+            s_vx[i] = (int)(k & 1023ull) - 512;
+            s_vy[i] = (int)((k >> 10) & 1023ull) - 512;
+          }
         }
+        __syncthreads();
       }
-      __syncthreads();
     }
 
     // ---- phase C: AMM sum and motion-compensated sums over the tile's pixels --
@@ -375,38 +455,102 @@ pair_kernel(const PairBatch b) {
       const int xs = bx0 * B0, ys = by0 * B0;
       const int xe = (bx0 + TBX >= nbx) ? W : (bx0 + TBX) * B0;
       const int ye = (by0 + TBY >= nby) ? H : (by0 + TBY) * B0;
-      const int nwx = (xe - xs + 3) >> 2;
-      const int nrows = ye - ys;
       const int lim_w = min(J0.w, J0.pitch);
       uint32_t si = 0, sj = 0, sii = 0, sjj = 0, sij = 0, sab = 0;
-      for (int idx = tid; idx < nrows * nwx; idx += NT) {
-        const int ry = idx / nwx, wx = idx - ry * nwx;
-        const int y = ys + ry, x = xs + 4 * wx;
-        const int bx = min(x / B0, nbx - 1), by = min(y / B0, nby - 1);
-        const int bl = (by - by0) * TBX + (bx - bx0);
-        const int vx = s_vx[bl], vy = s_vy[bl];
-        const uint8_t* irow = I0.p + (size_t)y * I0.pitch;
-        const int yj = clampi(y + vy, 0, H - 1);
-        const uint8_t* jrow = J0.p + (size_t)yj * J0.pitch;
-        const int xj = x + vx;
-        uint32_t iv, jv;
-        if (x + 3 <= W - 1) {
-          iv = __ldg(reinterpret_cast<const uint32_t*>(irow + x));
-          jv = (xj >= 0 && xj + 7 <= lim_w - 1) ? load4_unaligned(jrow, xj) : load4_clamped(jrow, xj, J0.w);
-        } else {
-          // ragged right edge: bytes beyond W contribute zero to every sum
-          iv = 0; jv = 0;
-          for (int k = 0; x + k < W; k++) {
-            iv |= (uint32_t)irow[x + k] << (8 * k);
-            jv |= (uint32_t)jrow[clampi(xj + k, 0, W - 1)] << (8 * k);
+      if (B0 == 16) {
+        // columns of 16 pixels: TBX block columns plus a possible ragged strip
+        constexpr int NCOL = TBX + 1, NGRP = NT / NCOL;
+        const int col = tid % NCOL, grp = tid / NCOL;
+        const int x = xs + 16 * col;
+        if (grp < NGRP && x < xe) {
+          const int bx = min(x >> 4, nbx - 1);
+          const int nx = min(16, xe - x);          // pixels of this column (16 except a ragged edge)
+          for (int y = ys + grp; y < ye; y += NGRP) {
+            const int by = min(y >> 4, nby - 1);
+            const int bl = (by - by0) * TBX + (bx - bx0);
+            const int vx = s_vx[bl], vy = s_vy[bl];
+            const uint8_t* irow = I0.p + (size_t)y * I0.pitch;
+            const uint8_t* jrow = J0.p + (size_t)clampi(y + vy, 0, H - 1) * J0.pitch;
+            const int xj = x + vx;
+            uint32_t iv[4], jv[4];
+            if (nx == 16) {
+              uint4 q;
+              if (fast && bx - bx0 < TBX && bx == (x >> 4) && y - ys < TBY * 16 && by == (y >> 4))
+                q = *reinterpret_cast<const uint4*>(s_i0 + ((y - ys) * TBX + (bx - bx0)) * 4);
+              else
+                q = __ldg(reinterpret_cast<const uint4*>(irow + x));
+              iv[0] = q.x; iv[1] = q.y; iv[2] = q.z; iv[3] = q.w;
+              if (xj >= 0 && xj + 19 <= lim_w - 1) {
+                const uint32_t* p = reinterpret_cast<const uint32_t*>(jrow + (xj & ~3));
+                const uint32_t a0 = __ldg(p), a1 = __ldg(p + 1), a2 = __ldg(p + 2), a3 = __ldg(p + 3), a4 = __ldg(p + 4);
+                const int sh = 8 * (xj & 3);
+                jv[0] = __funnelshift_r(a0, a1, sh);
+                jv[1] = __funnelshift_r(a1, a2, sh);
+                jv[2] = __funnelshift_r(a2, a3, sh);
+                jv[3] = __funnelshift_r(a3, a4, sh);
+              } else {
+#pragma unroll
+                for (int k = 0; k < 4; k++) jv[k] = load4_clamped(jrow, xj + 4 * k, W);
+              }
+            } else {
+              // ragged right edge: bytes beyond W contribute zero to every sum
+#pragma unroll
+              for (int kw = 0; kw < 4; kw++) {
+                uint32_t a = 0, c = 0;
+#pragma unroll
+                for (int kb = 0; kb < 4; kb++) {
+                  const int k = 4 * kw + kb;
+                  if (k < nx) {
+                    a |= (uint32_t)irow[x + k] << (8 * kb);
+                    c |= (uint32_t)jrow[clampi(xj + k, 0, W - 1)] << (8 * kb);
+                  }
+                }
+                iv[kw] = a;
+                jv[kw] = c;
+              }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+              si = __dp4a(iv[k], 0x01010101u, si);
+              sj = __dp4a(jv[k], 0x01010101u, sj);
+              sii = __dp4a(iv[k], iv[k], sii);
+              sjj = __dp4a(jv[k], jv[k], sjj);
+              sij = __dp4a(iv[k], jv[k], sij);
+              sab = sad4(iv[k], jv[k], sab);
+            }
           }
         }
-        si = __dp4a(iv, 0x01010101u, si);
-        sj = __dp4a(jv, 0x01010101u, sj);
-        sii = __dp4a(iv, iv, sii);
-        sjj = __dp4a(jv, jv, sjj);
-        sij = __dp4a(iv, jv, sij);
-        sab = sad4(iv, jv, sab);
+      } else {
+        const int nwx = (xe - xs + 3) >> 2;
+        const int nrows = ye - ys;
+        for (int idx = tid; idx < nrows * nwx; idx += NT) {
+          const int ry = idx / nwx, wx = idx - ry * nwx;
+          const int y = ys + ry, x = xs + 4 * wx;
+          const int bx = min(x / B0, nbx - 1), by = min(y / B0, nby - 1);
+          const int bl = (by - by0) * TBX + (bx - bx0);
+          const int vx = s_vx[bl], vy = s_vy[bl];
+          const uint8_t* irow = I0.p + (size_t)y * I0.pitch;
+          const int yj = clampi(y + vy, 0, H - 1);
+          const uint8_t* jrow = J0.p + (size_t)yj * J0.pitch;
+          const int xj = x + vx;
+          uint32_t iv, jv;
+          if (x + 3 <= W - 1) {
+            iv = __ldg(reinterpret_cast<const uint32_t*>(irow + x));
+            jv = (xj >= 0 && xj + 7 <= lim_w - 1) ? load4_unaligned(jrow, xj) : load4_clamped(jrow, xj, J0.w);
+          } else {
+            iv = 0; jv = 0;
+            for (int k = 0; x + k < W; k++) {
+              iv |= (uint32_t)irow[x + k] << (8 * k);
+              jv |= (uint32_t)jrow[clampi(xj + k, 0, W - 1)] << (8 * k);
+            }
+          }
+          si = __dp4a(iv, 0x01010101u, si);
+          sj = __dp4a(jv, 0x01010101u, sj);
+          sii = __dp4a(iv, iv, sii);
+          sjj = __dp4a(jv, jv, sjj);
+          sij = __dp4a(iv, jv, sij);
+          sab = sad4(iv, jv, sab);
+        }
       }
       // AMM: one term per block of the tile, from the exact table
       uint32_t samm = 0;
