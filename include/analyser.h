@@ -197,6 +197,26 @@ int analyser_measure_pairs(const analyser_params* p, int width, int height, cons
                            int64_t* records, int16_t* motion, void* stream);
 
 /*
+ * One pair measure that allocates no device memory: the same record as
+ * analyser_measure_pairs (7 int64 written to HOST memory `record`) for frames
+ * a and b in DEVICE memory (pitch_bytes a multiple of 16, 16-byte aligned
+ * pointers) and pair kind `kind`.  The paper has no counterpart; it exists for
+ * callers embedded in a host application that reserves all device memory up
+ * front and forbids cudaMalloc/cudaFree while it runs (an allocation could
+ * fail against that reservation, and both calls synchronise the device).
+ * Its scratch (pyramids, descriptors, accumulators) is a fixed 5.5 MiB device
+ * array inside this library, present on every device that loads it until the
+ * process exits: 3840x2160 frames fit, larger scratch needs are rejected with
+ * ANALYSER_ERR_INVALID_ARG.  Only params levels = 3, block = 16.  The array is
+ * shared by all calls: calls whose GPU work overlaps race on it.  The first
+ * call with a given device current looks up the array's device address; make
+ * it before any stream capture.  Returns after the record is in `record`.
+ */
+int analyser_measure_pair_noalloc(const analyser_params* p, int width, int height, int kind,
+                                  const uint8_t* frame_a, const uint8_t* frame_b, long long pitch_bytes,
+                                  int64_t* record, void* stream);
+
+/*
  * Host-only: run the detectors alone on measures supplied by `get`, without a
  * GPU.  get(ctx, kind, a, b, rec) fills rec[0..8] = sum i, sum j, sum i^2,
  * sum j^2, sum i*j, sum |i-j|, S_amm, n, nb for pair (kind, a, b) and returns 0

@@ -84,6 +84,7 @@ SIGNATURES = {
     "analyser_destroy": (None, [VP]),
     "analyser_measure_pairs": (c_int, [P(Params), c_int, c_int, VP, c_ll, c_ll, c_int, P(c_int), P(c_int),
                                        P(c_int), c_int, P(c_i64), P(ctypes.c_int16), VP]),
+    "analyser_measure_pair_noalloc": (c_int, [P(Params), c_int, c_int, c_int, VP, VP, c_ll, P(c_i64), VP]),
     "analyser_detect_offline": (c_int, [P(Params), c_int, c_int, c_int, MEASURE_FN, VP, P(VP)]),
     "analyser_measure_sad_peak": (c_int, [c_int, P(c_double)]),
     "server_create": (c_int, [P(Params), c_ull, P(VP)]),

@@ -293,7 +293,7 @@ def _place_events(rng, nframes, gap_range, n_dissolves, dis_len, flash_every, gu
         else:
             cuts.append(b)
     flashes = []
-    if flash_every:
+    if flash_every and nframes > 2 * guard + 1:
         busy = []
         for c in cuts:
             busy.append((c - 1, c))
