@@ -203,6 +203,125 @@ def run_kernel(args):
     return 0
 
 
+def _gen_clip(spec):
+    from paper_2502_09202_gb300 import synth
+    return synth.Clip(spec).frames()
+
+
+def _gen_clips(specs):
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    with ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 4), mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_gen_clip, specs))
+
+
+def _same_decisions(a, b):
+    keys = ("cuts", "dissolves", "keyframes", "shots", "label", "field_order", "pulldown_phase")
+    return all(a[k] == b[k] for k in keys) and a["measures"] == b["measures"]
+
+
+def _warm_tiles(api, sizes):
+    # the tile autotune runs once per resolution and process; keep it out of the timed region
+    for w, h in sorted(set(sizes)):
+        a = api.Analyser(w, h, 25.0)
+        a.close()
+
+
+def run_batched(args):
+    """Batched workload (uneven clips, every structure, several resolutions): the
+    plain path analyses clip after clip; the batched path runs them all through
+    one server, whose GPU waves and launches carry every active clip's work."""
+    import torch
+    from paper_2502_09202_gb300 import api, synth
+    torch.cuda.set_device(0)
+    lo, hi = int(60 * args.length_scale), int(600 * args.length_scale)
+    specs = synth.config_batched(nclips=args.clips, length_range=(max(lo, 8), max(hi, 9)))
+    clips = _gen_clips(specs)
+    frames = sum(len(c) for c in clips)
+    _warm_tiles(api, [(s.width, s.height) for s in specs])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = []
+    launches_plain = 0
+    for s, f in zip(specs, clips):
+        with api.Analyser(s.width, s.height, s.fps) as a:
+            a.push(f)
+            a.finish()
+            plain.append(a.results())
+            launches_plain += a.stats()["launches"]
+    t_plain = time.perf_counter() - t0
+    srv = api.Server(budget_bytes=int(args.budget_gb * (1 << 30)))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tickets = [srv.submit(f, s.fps) for s, f in zip(specs, clips)]
+    srv.drain()
+    t_batched = time.perf_counter() - t0
+    prof = srv.profile()
+    same = all(_same_decisions(srv.poll(t), p) for t, p in zip(tickets, plain))
+    srv.close()
+    print(json.dumps({
+        "mode": "batched", "metric": "frames/s (host frames in, results out)", "unit": "frames/s",
+        "clips": len(specs), "frames": frames, "pixels": sum(s.pixels * s.nframes for s in specs),
+        "length_range": [lo, hi], "resolutions": sorted({f"{s.width}x{s.height}" for s in specs}),
+        "plain": {"value": frames / t_plain, "seconds": t_plain, "launches": launches_plain},
+        "batched": {"value": frames / t_batched, "seconds": t_batched, "launches": prof["launches"],
+                    "waves": prof["waves"], "pairs": prof["pairs"]},
+        "speedup": t_plain / t_batched, "identical_outputs": same}))
+    return 0
+
+
+def run_served(args):
+    """Served workload: clip requests with Poisson arrivals, admitted by a device
+    memory budget and batched continuously; reports throughput and the per-clip
+    latency from arrival to results."""
+    import numpy as np
+    import torch
+    from paper_2502_09202_gb300 import api, synth
+    torch.cuda.set_device(0)
+    lo, hi = int(30 * args.length_scale), int(300 * args.length_scale)
+    reqs = synth.config_served(nrequests=args.requests, rate_hz=args.rate, length_range=(max(lo, 8), max(hi, 9)))
+    clips = _gen_clips([s for _, s in reqs])
+    frames = sum(len(c) for c in clips)
+    _warm_tiles(api, [(s.width, s.height) for _, s in reqs])
+    srv = api.Server(budget_bytes=int(args.budget_gb * (1 << 30)))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pending = list(range(len(reqs)))
+    tickets = {}
+    active = 0
+    while pending or active:
+        now = time.perf_counter() - t0
+        while pending and reqs[pending[0]][0] <= now:
+            i = pending.pop(0)
+            tickets[i] = srv.submit(clips[i], reqs[i][1].fps)
+        if tickets:
+            active = srv.step()
+        if not active and pending:
+            time.sleep(max(0.0, min(0.002, reqs[pending[0]][0] - (time.perf_counter() - t0))))
+    t_total = time.perf_counter() - t0
+    lat = np.array([srv.latency(tickets[i]) for i in range(len(reqs))])
+    # every result equals the same clip analysed alone
+    check = list(range(0, len(reqs), max(1, len(reqs) // 8)))
+    same = True
+    for i in check:
+        s = reqs[i][1]
+        with api.Analyser(s.width, s.height, s.fps) as a:
+            a.push(clips[i])
+            a.finish()
+            same = same and _same_decisions(a.results(), srv.poll(tickets[i]))
+    prof = srv.profile()
+    srv.close()
+    print(json.dumps({
+        "mode": "served", "metric": "frames/s and per-clip latency (arrival to results)", "unit": "frames/s",
+        "requests": len(reqs), "rate_hz": args.rate, "frames": frames, "length_range": [lo, hi],
+        "value": frames / t_total, "seconds": t_total, "last_arrival_s": reqs[-1][0],
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "max": float(lat.max())},
+        "waves": prof["waves"], "launches": prof["launches"], "pairs": prof["pairs"],
+        "identical_to_alone": same, "checked": len(check)}))
+    return 0
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -335,13 +454,22 @@ def main():
     ap.add_argument("--ref-frames", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--window", type=int, default=256, help="frames resident per clip")
-    ap.add_argument("--mode", default="clip", choices=["clip", "kernel"])
+    ap.add_argument("--mode", default="clip", choices=["clip", "kernel", "batched", "served"])
+    ap.add_argument("--clips", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=512)
+    ap.add_argument("--rate", type=float, default=40.0)
+    ap.add_argument("--length-scale", type=float, default=1.0)
+    ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--pairs", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "kernel":
         return run_kernel(args)
+    if args.mode == "batched":
+        return run_batched(args)
+    if args.mode == "served":
+        return run_served(args)
     return run_gpu(args)
 
 
