@@ -208,11 +208,16 @@ def _gen_clip(spec):
     return synth.Clip(spec).frames()
 
 
-def _gen_clips(specs):
+def _gen_clips(specs, pin=True):
+    """Clips as host arrays; pinned (page-locked) like a serving front end's buffers."""
     import multiprocessing as mp
     from concurrent.futures import ProcessPoolExecutor
     with ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 4), mp_context=mp.get_context("spawn")) as ex:
-        return list(ex.map(_gen_clip, specs))
+        out = list(ex.map(_gen_clip, specs))
+    if pin:
+        import torch
+        out = [torch.from_numpy(c).pin_memory().numpy() for c in out]
+    return out
 
 
 def _same_decisions(a, b):

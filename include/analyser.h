@@ -91,6 +91,7 @@ typedef struct {
   int tile_x, tile_y;                  /* pair-kernel tile in blocks (8x4, 4x4, 8x2, 16x2, 4x8);
                                           0 = autotuned per resolution (0, 0) */
   int time_kernels;                    /* record CUDA events around every kernel launch (0) */
+  int step_frames;                     /* server: frames copied per clip per step (0 = fill the window) (32) */
 } analyser_params;
 
 /* One measure of one pair, in the order of (kind, a, b). */

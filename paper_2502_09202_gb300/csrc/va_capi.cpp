@@ -107,6 +107,7 @@ int analyser_default_params(analyser_params* p) {
   p->tile_x = 0;
   p->tile_y = 0;
   p->time_kernels = 0;
+  p->step_frames = 32;
   return ANALYSER_OK;
 }
 
@@ -383,8 +384,9 @@ int server_step(server* s, int* active) {
     server::Req& r = kv.second;
     if (!r.admitted || r.done) continue;
     if (r.uploaded < r.nframes) {
-      const int k = e.upload_host(r.clip.get(), r.frames + (size_t)r.uploaded * r.clip->geo.H * r.pitch, r.pitch,
-                                  r.nframes - r.uploaded);
+      int n = r.nframes - r.uploaded;
+      if (s->p.step_frames > 0 && n > s->p.step_frames) n = s->p.step_frames;
+      const int k = e.upload_host(r.clip.get(), r.frames + (size_t)r.uploaded * r.clip->geo.H * r.pitch, r.pitch, n);
       if (k < 0) return fail_srv(s, e.status, e.message);
       r.uploaded += k;
     }

@@ -67,6 +67,10 @@ int validate_params(const analyser_params& p, std::string& why) {
     why = "tile_x x tile_y is not a compiled tile shape";
     return ANALYSER_ERR_INVALID_ARG;
   }
+  if (p.step_frames < 0) {
+    why = "step_frames must be >= 0";
+    return ANALYSER_ERR_INVALID_ARG;
+  }
   if (p.window_frames != 0 && p.window_frames < 2 * p.kmax + 6) {
     why = "window_frames must be 0 (auto) or >= 2*kmax+6";
     return ANALYSER_ERR_INVALID_ARG;
