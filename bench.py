@@ -436,6 +436,8 @@ def run_gpu(args):
                      "kernel_ms_per_step": pair_ms / args.steps, "pyramid_ms_per_step": pyr_ms / args.steps,
                      "peak_source": "measured live: analyser_measure_sad_peak (vabsdiff4.add register loop)",
                      "hbm_peak_gbs": peaks.get("hbm_gbs")},
+        "host_ms_per_step": {k: sum(p[k] for p in profs) / args.steps for k in
+                             ("host_gather_ms", "host_wait_ms", "host_results_ms", "host_setup_ms")},
         "clocks": clk.summary(),
     }
     if hres["cuts"] != res["cuts"] or hres["dissolves"] != res["dissolves"]:

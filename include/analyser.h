@@ -178,6 +178,10 @@ typedef struct {
   double absdiff_ops;                        /* algorithmic |a-b| accumulates of the block search */
   double pyramid_bytes;                      /* algorithmic bytes of the pyramid kernel (read + write) */
   long long h2d_bytes, d2h_bytes;            /* host<->device bytes moved by the library */
+  double host_gather_ms;                     /* host time building wave descriptors */
+  double host_wait_ms;                       /* host time waiting for wave completion */
+  double host_results_ms;                    /* host time finalising records and running detectors */
+  double host_setup_ms;                      /* host time creating the analyser (window allocation, tables) */
 } analyser_profile_t;
 int analyser_profile(const analyser* a, analyser_profile_t* out);
 

@@ -113,6 +113,7 @@ int analyser_default_params(analyser_params* p) {
 
 int analyser_create(int width, int height, double fps, const analyser_params* p, analyser** out) {
   if (!p || !out) return ANALYSER_ERR_INVALID_ARG;
+  const double t0 = va::now_seconds();
   *out = nullptr;
   std::string why;
   int rc = va::validate_params(*p, why);
@@ -134,6 +135,7 @@ int analyser_create(int width, int height, double fps, const analyser_params* p,
     delete a;
     return rc;
   }
+  a->eng->host_setup_ms += 1e3 * (va::now_seconds() - t0);
   *out = a;
   return ANALYSER_OK;
 }
@@ -146,25 +148,34 @@ int analyser_push_frames(analyser* a, const uint8_t* luma, long long pitch_bytes
   if (nframes < 0 || (nframes > 0 && !luma) || pitch_bytes < a->clip.geo.W) return ANALYSER_ERR_INVALID_ARG;
   if (a->clip.external_l0) return fail(a, ANALYSER_ERR_STATE, "host and device pushes cannot be mixed");
   va::Engine& e = *a->eng;
+  // pipeline: copy a first chunk, then repeatedly launch a wave on what is
+  // resident, copy the next chunk into free slots while it runs, and complete it
   int done = 0;
-  while (done < nframes) {
+  int stall = 0;
+  // half a window per copy, so that one half can be copied while the other computes
+  const int chunk = a->clip.cap / 2 > 0 ? a->clip.cap / 2 : 1;
+  auto copy_next = [&]() -> int {
     const int k = e.upload_host(&a->clip, luma + (size_t)done * a->clip.geo.H * pitch_bytes, pitch_bytes,
-                                nframes - done);
-    if (k < 0 || e.status) return fail(a, e.status ? e.status : ANALYSER_ERR_CUDA, e.message);
+                                std::min(nframes - done, chunk));
+    if (k < 0 || e.status) return -1;
     done += k;
-    if (done < nframes) {
-      const int before = e.free_slots(&a->clip);
-      const int rc = drive(a, false);
-      if (rc) return rc;
-      if (e.free_slots(&a->clip) == 0 && before == 0) {
-        const int rc2 = e.wave();
-        if (rc2 < 0) return fail(a, e.status, e.message);
-        if (e.free_slots(&a->clip) == 0) return fail(a, ANALYSER_ERR_STATE, "frame window cannot advance");
-      }
+    return k;
+  };
+  if (copy_next() < 0) return fail(a, e.status ? e.status : ANALYSER_ERR_CUDA, e.message);
+  while (done < nframes) {
+    const int launched = e.wave_launch();
+    if (launched < 0 || e.status) return fail(a, e.status ? e.status : launched, e.message);
+    const int k = copy_next();
+    if (k < 0) return fail(a, e.status ? e.status : ANALYSER_ERR_CUDA, e.message);
+    if (launched > 0) {
+      const int rc = e.wave_complete();
+      if (rc < 0 || e.status) return fail(a, e.status ? e.status : rc, e.message);
     }
+    if (launched > 0 || k > 0) stall = 0;
+    else if (++stall > 2) return fail(a, ANALYSER_ERR_STATE, "frame window cannot advance");
   }
   // the caller may reuse its buffer once this returns
-  if (cudaStreamSynchronize(e.stream) != cudaSuccess) return fail(a, ANALYSER_ERR_CUDA, "cudaStreamSynchronize");
+  if (e.sync_uploads()) return fail(a, ANALYSER_ERR_CUDA, "cudaStreamSynchronize(copies)");
   return ANALYSER_OK;
 }
 

@@ -103,7 +103,8 @@ void Geometry::init(int width, int height, int levels, bool own_l0) {
   for (int l = 1; l < L; l++) { off_f[l] = off; off += round_up_sz((size_t)fh[l] * fp[l] + 16, 256); }
   for (int l = 1; l < L; l++) { off_u[l] = off; off += round_up_sz((size_t)gh[l] * gp[l] + 16, 256); }
   for (int l = 1; l < L; l++) { off_l[l] = off; off += round_up_sz((size_t)gh[l] * gp[l] + 16, 256); }
-  slot_bytes = off;
+  // a whole number of level-0 rows, so that consecutive slots form one pitched 3D copy target
+  slot_bytes = own_l0 ? round_up_sz(off, (size_t)fp[0] * 4) : off;
 }
 
 Engine::Engine(const analyser_params& params) : p(params) {}
@@ -122,6 +123,8 @@ Engine::~Engine() {
   if (d_vec) cudaFree(d_vec);
   for (cudaEvent_t& e : ev_)
     if (e) cudaEventDestroy(e);
+  if (ev_up_) cudaEventDestroy(ev_up_);
+  if (cstream) cudaStreamDestroy(cstream);
   if (stream) cudaStreamDestroy(stream);
 }
 
@@ -137,6 +140,10 @@ void Engine::profile(analyser_profile_t* out) const {
   out->pyramid_bytes = pyr_bytes;
   out->h2d_bytes = h2d_bytes;
   out->d2h_bytes = d2h_bytes;
+  out->host_gather_ms = host_gather_ms;
+  out->host_wait_ms = host_wait_ms;
+  out->host_results_ms = host_results_ms;
+  out->host_setup_ms = host_setup_ms;
 }
 
 int Engine::init(std::string& why) {
@@ -144,6 +151,8 @@ int Engine::init(std::string& why) {
   if (rc) return rc;
   VA_CUDA_TRY(cudaSetDevice(p.device), why);
   VA_CUDA_TRY(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking), why);
+  VA_CUDA_TRY(cudaStreamCreateWithFlags(&cstream, cudaStreamNonBlocking), why);
+  VA_CUDA_TRY(cudaEventCreateWithFlags(&ev_up_, cudaEventDisableTiming), why);
   VA_CUDA_TRY(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, p.device), why);
   // Q(k) = floor(sqrt(k) * 2^16) for every k = vx^2 + vy^2 the search can produce
   int vmax = p.radius_coarse;
@@ -207,21 +216,34 @@ void Engine::remove_clip(Clip* c) {
 int Engine::upload_host(Clip* c, const uint8_t* frames, long long pitch, int nframes) {
   const int k = std::min(nframes, free_slots(c));
   const Geometry& g = c->geo;
-  for (int i = 0; i < k; i++) {
-    const int f = c->pushed + i;
-    const int s = c->slot_of(f);
-    uint8_t* dst = c->d_ring + (size_t)s * g.slot_bytes;
-    cudaError_t e = cudaMemcpy2DAsync(dst, g.fp[0], frames + (size_t)i * g.H * pitch, pitch, g.W, g.H,
-                                      cudaMemcpyHostToDevice, stream);
+  // one 3D copy per run of consecutive slots: frames are `H*pitch` apart in
+  // host memory and `slot_bytes` (a whole number of level-0 rows) apart in the ring
+  int i = 0;
+  while (i < k) {
+    const int s0 = c->slot_of(c->pushed + i);
+    const int run = std::min(k - i, c->cap - s0);
+    cudaMemcpy3DParms cp = {};
+    cp.srcPtr = make_cudaPitchedPtr(const_cast<uint8_t*>(frames + (size_t)i * g.H * pitch), (size_t)pitch, g.W, g.H);
+    cp.dstPtr = make_cudaPitchedPtr(c->d_ring + (size_t)s0 * g.slot_bytes, (size_t)g.fp[0], g.W, g.slot_bytes / g.fp[0]);
+    cp.extent = make_cudaExtent(g.W, g.H, run);
+    cp.kind = cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpy3DAsync(&cp, cstream);
     if (e != cudaSuccess) {
       status = ANALYSER_ERR_CUDA;
-      message = std::string("cudaMemcpy2DAsync(frame): ") + cudaGetErrorString(e);
+      message = std::string("cudaMemcpy3DAsync(frames): ") + cudaGetErrorString(e);
       return -1;
     }
-    c->l0[s] = dst;
-    c->l0_pitch[s] = g.fp[0];
+    for (int j = 0; j < run; j++) {
+      c->l0[s0 + j] = c->d_ring + (size_t)(s0 + j) * g.slot_bytes;
+      c->l0_pitch[s0 + j] = g.fp[0];
+    }
+    i += run;
   }
   h2d_bytes += (long long)k * g.W * g.H;
+  if (k > 0) {
+    cudaEventRecord(ev_up_, cstream);
+    up_pending_ = true;
+  }
   c->pushed += k;
   return k;
 }
@@ -402,7 +424,15 @@ int Engine::setup_pair_job(const Clip& c, uint64_t key, PairJob& pj, int item_be
 }
 
 int Engine::wave() {
+  const int n = wave_launch();
+  if (n <= 0) return n;
+  return wave_complete();
+}
+
+int Engine::wave_launch() {
   if (status) return status;
+  if (inflight_) return ANALYSER_ERR_STATE;
+  const double tw0 = now_seconds();
   wp_.clear();
   // detectors with nothing queued may be able to move on (new frames, finish)
   for (Clip* c : clips) {
@@ -451,6 +481,12 @@ int Engine::wave() {
   for (int l = 1; l < kMaxLevels; l++) ndown += (int)down[l].size();
   const int npairs = (int)wp_.size();
   if (npairs == 0 && ndown == 0) return 0;
+  if (up_pending_) {
+    // frames copied on the copy stream must land before their pyramids
+    cudaError_t we = cudaStreamWaitEvent(stream, ev_up_, 0);
+    if (we) { status = ANALYSER_ERR_CUDA; message = "cudaStreamWaitEvent(upload)"; return status; }
+    up_pending_ = false;
+  }
   if (ensure_capacity(npairs, ndown)) { status = ANALYSER_ERR_CUDA; return status; }
 
   // ---- pair jobs, grouped by tile shape ---------------------------------------
@@ -505,6 +541,8 @@ int Engine::wave() {
   }
 
   // ---- launch -----------------------------------------------------------------
+  const double tw1 = now_seconds();
+  host_gather_ms += 1e3 * (tw1 - tw0);
   std::string& why = message;
   auto fail = [&](cudaError_t e, const char* what) {
     status = ANALYSER_ERR_CUDA;
@@ -566,15 +604,42 @@ int Engine::wave() {
   }
   e = cudaMemcpyAsync(h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, stream);
   if (e) return fail(e, "cudaMemcpyAsync(status)");
+  fl_npairs_ = npairs;
+  fl_ndown_ = ndown;
+  fl_vec_total_ = vec_total;
+  fl_groups_ = !groups.empty();
+  fl_t1_ = tw1;
+  inflight_ = true;
+  return npairs + ndown;
+}
+
+int Engine::wave_complete() {
+  if (!inflight_) return 0;
+  inflight_ = false;
+  const int npairs = fl_npairs_, ndown = fl_ndown_;
+  const size_t vec_total = fl_vec_total_;
+  const bool any_groups = fl_groups_;
+  const double tw1 = fl_t1_;
+  const bool timed = p.time_kernels != 0;
+  auto fail = [&](cudaError_t e, const char* what) {
+    status = ANALYSER_ERR_CUDA;
+    message = std::string(what) + ": " + cudaGetErrorString(e);
+    return status;
+  };
+  cudaError_t e;
+  const double tw2 = now_seconds();
   e = cudaStreamSynchronize(stream);
   if (e) return fail(e, "cudaStreamSynchronize(wave)");
+  const double tw3 = now_seconds();
+  host_wait_ms += 1e3 * (tw3 - tw2);
+  host_gather_ms += 1e3 * (tw2 - tw1);
   const int dev_status = *h_status;
   h2d_bytes += (long long)(sizeof(PairJob) * npairs + sizeof(DownJob) * ndown);
   d2h_bytes += (long long)(sizeof(unsigned long long) * kRecWords * npairs + sizeof(short2) * vec_total + sizeof(int));
   if (timed) {
     float ms = 0.f;
     if (ndown && cudaEventElapsedTime(&ms, ev_[0], ev_[1]) == cudaSuccess) pyr_ms += ms;
-    if (!groups.empty() && cudaEventElapsedTime(&ms, ev_[2], ev_[3]) == cudaSuccess) pair_ms += ms;
+    if (any_groups && cudaEventElapsedTime(&ms, ev_[2], ev_[3]) == cudaSuccess) pair_ms += ms;
   }
   // algorithmic block-search work: |a-b| accumulates per block over all levels
   {
@@ -636,6 +701,7 @@ int Engine::wave() {
     if (c->done()) c->evicted = c->pushed;
     else c->evicted = std::max(c->evicted, std::min(keep, c->pushed));
   }
+  host_results_ms += 1e3 * (now_seconds() - tw3);
   return npairs + ndown;
 }
 

@@ -101,7 +101,13 @@ class Engine {
   // readback, detector advance, eviction.  Returns the number of pairs run
   // (0 = nothing to do), or a negative error.
   int wave();
+  // the same in two halves, so that host work (e.g. copying the next frames on
+  // the copy stream) can overlap the GPU work of a wave
+  int wave_launch();
+  int wave_complete();
+  bool wave_inflight() const { return inflight_; }
   int free_slots(const Clip* c) const { return c->cap - (c->pushed - c->evicted); }
+  int sync_uploads() { return cudaStreamSynchronize(cstream) == cudaSuccess ? 0 : ANALYSER_ERR_CUDA; }
 
   // stateless measure for tests and timing
   int measure_pairs(int width, int height, const uint8_t* frames, long long pitch, long long stride, int nframes,
@@ -113,11 +119,13 @@ class Engine {
 
   analyser_params p;
   std::vector<Clip*> clips;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;    // kernels and record read-back
+  cudaStream_t cstream = nullptr;   // host-to-device frame copies
   long long n_pairs = 0, n_waves = 0, n_launches = 0;
   long long n_pair_launches = 0, n_pyr_launches = 0;
   double pair_ms = 0.0, pyr_ms = 0.0, absdiff_ops = 0.0, pyr_bytes = 0.0;
   long long h2d_bytes = 0, d2h_bytes = 0;
+  double host_gather_ms = 0, host_wait_ms = 0, host_results_ms = 0, host_setup_ms = 0;
   void profile(analyser_profile_t* out) const;
   int status = ANALYSER_OK;
   std::string message;
@@ -135,6 +143,14 @@ class Engine {
   int* d_status = nullptr;
   int* h_status = nullptr;
   cudaEvent_t ev_[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_up_ = nullptr;     // last frame copy
+  bool up_pending_ = false;
+  // wave in flight (between wave_launch and wave_complete)
+  bool inflight_ = false;
+  int fl_npairs_ = 0, fl_ndown_ = 0;
+  size_t fl_vec_total_ = 0;
+  bool fl_groups_ = false;
+  double fl_t1_ = 0.0;
   int sm_count = 0;
   // wave buffers
   int cap_pairs = 0, cap_down = 0;
