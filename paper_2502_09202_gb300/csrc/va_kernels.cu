@@ -104,7 +104,12 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem));
 }
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait_group1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Refinement of every block of a tile at one pyramid level (block side S,
@@ -255,18 +260,20 @@ pair_kernel(const PairBatch b) {
   constexpr int G = S::G, NB = S::NB, NT = S::NT, WROWS = S::WROWS, WWORDS = S::WWORDS;
   static_assert(R % 4 == 0 && R <= 31, "coarse radius");
 
-  __shared__ uint32_t s_jwin[WROWS][WWORDS];
-  __shared__ uint32_t s_iw[TBY * kCoarseSide][TBX];
+  // inputs of a tile, double-buffered: the next tile's are copied (cp.async)
+  // while the current one computes
+  __shared__ __align__(16) uint32_t s_jwin[2][WROWS * WWORDS];
+  __shared__ __align__(16) uint32_t s_iw[2][TBY * kCoarseSide * TBX];
   __shared__ uint32_t s_best32[NB];
   __shared__ unsigned long long s_best64[NB];
   __shared__ int s_vx[NB], s_vy[NB];
   __shared__ unsigned long long s_red[S::NW][kRecWords];
-  __shared__ PairJob s_job;
+  __shared__ PairJob s_job[2];
   // refinement windows: level side 16 with radius 2 is the largest fast case
   __shared__ uint32_t s_win[NB * 20 * 6];
   // I tiles of levels 0 and 1 (fast path: 3 levels, radius 2), staged asynchronously
-  __shared__ __align__(16) uint32_t s_i0[TBY * 16 * TBX * 4];
-  __shared__ __align__(16) uint32_t s_i1[TBY * 8 * TBX * 2];
+  __shared__ __align__(16) uint32_t s_i0[2][TBY * 16 * TBX * 4];
+  __shared__ __align__(16) uint32_t s_i1[2][TBY * 8 * TBX * 2];
 
   const int tid = threadIdx.x;
   const int L = b.cfg.levels;
@@ -275,62 +282,96 @@ pair_kernel(const PairBatch b) {
   const int rr = b.cfg.refine;
   const int side = 2 * rr + 1, ncand = side * side;
 
-  for (int item = blockIdx.x; item < b.nitems; item += gridDim.x) {
-    // ---- locate the job owning this tile ------------------------------------
+  const bool fast = (L == 3 && rr == 2);
+  auto load_job = [&](int item, int slot) {
     int lo = 0, hi = b.njobs - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (b.jobs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
     }
-    {
-      static_assert(sizeof(PairJob) % 4 == 0, "job copy");
-      const int* src = reinterpret_cast<const int*>(b.jobs + lo);
-      int* dst = reinterpret_cast<int*>(&s_job);
-      for (int i = tid; i < (int)(sizeof(PairJob) / 4); i += NT) dst[i] = src[i];
-    }
-    __syncthreads();
-    const PairJob& jb = s_job;
+    static_assert(sizeof(PairJob) % 4 == 0, "job copy");
+    const int* src = reinterpret_cast<const int*>(b.jobs + lo);
+    int* dst = reinterpret_cast<int*>(&s_job[slot]);
+    for (int i = tid; i < (int)(sizeof(PairJob) / 4); i += NT) dst[i] = src[i];
+  };
+  auto tile_of = [&](const PairJob& jb, int item, int& bx0, int& by0) {
     const int local = item - jb.item_begin;
-    const int bx0 = (local % jb.tiles_x) * TBX, by0 = (local / jb.tiles_x) * TBY;
-    const int nbx = jb.nbx, nby = jb.nby;
-    const bool fast = (L == 3 && rr == 2);
+    bx0 = (local % jb.tiles_x) * TBX;
+    by0 = (local / jb.tiles_x) * TBY;
+  };
+  // asynchronous copies of a tile's inputs: the coarse search window (words
+  // inside the coarsest level; the others are filled clamp-to-edge before use),
+  // the coarse block rows and, for the default estimator, the level-0 and
+  // level-1 I tiles
+  auto prefetch = [&](int item, int slot) {
+    const PairJob& jb = s_job[slot];
+    int bx0, by0;
+    tile_of(jb, item, bx0, by0);
+    const Plane J2 = jb.J[L - 1], I2 = jb.I[L - 1];
+    const int Xw0 = bx0 * kCoarseSide - R, Yw0 = by0 * kCoarseSide - R;
+    for (int c = tid; c < WROWS * WWORDS; c += NT) {
+      const int wy = c / WWORDS, wx = c - wy * WWORDS;
+      const int y = Yw0 + wy, x = Xw0 + 4 * wx;
+      if (y >= 0 && y < J2.h && x >= 0 && x + 3 <= J2.w - 1)
+        cp_async4(&s_jwin[slot][c], J2.p + (size_t)y * J2.pitch + x);
+    }
+    for (int c = tid; c < TBY * kCoarseSide * TBX; c += NT) {
+      const int r = c / TBX, k = c - r * TBX;
+      if (bx0 + k < jb.nbx && by0 + r / kCoarseSide < jb.nby)
+        cp_async4(&s_iw[slot][c], I2.p + (size_t)(by0 * kCoarseSide + r) * I2.pitch + (bx0 + k) * kCoarseSide);
+    }
     if (fast) {
-      // I tiles of levels 0 and 1 for the refinement and the correlation sums:
-      // copied while the coarse search runs
       for (int c = tid; c < TBY * 16 * TBX; c += NT) {
         const int r = c / TBX, k = c - r * TBX;
-        if (bx0 + k < nbx && by0 + r / 16 < nby)
-          cp_async16(s_i0 + (r * TBX + k) * 4, jb.I[0].p + (size_t)(by0 * 16 + r) * jb.I[0].pitch + (bx0 + k) * 16);
+        if (bx0 + k < jb.nbx && by0 + r / 16 < jb.nby)
+          cp_async16(&s_i0[slot][c * 4], jb.I[0].p + (size_t)(by0 * 16 + r) * jb.I[0].pitch + (bx0 + k) * 16);
       }
       for (int c = tid; c < TBY * 8 * TBX; c += NT) {
         const int r = c / TBX, k = c - r * TBX;
-        if (bx0 + k < nbx && by0 + r / 8 < nby)
-          cp_async8(s_i1 + (r * TBX + k) * 2, jb.I[1].p + (size_t)(by0 * 8 + r) * jb.I[1].pitch + (bx0 + k) * 8);
+        if (bx0 + k < jb.nbx && by0 + r / 8 < jb.nby)
+          cp_async8(&s_i1[slot][c * 2], jb.I[1].p + (size_t)(by0 * 8 + r) * jb.I[1].pitch + (bx0 + k) * 8);
       }
-      cp_async_commit();
     }
+    cp_async_commit();
+  };
+
+  int slot = 0;
+  if ((int)blockIdx.x < b.nitems) {
+    load_job(blockIdx.x, 0);
+    __syncthreads();
+    prefetch(blockIdx.x, 0);
+  }
+  for (int item = blockIdx.x; item < b.nitems; item += gridDim.x, slot ^= 1) {
+    const int next = item + gridDim.x;
+    if (next < b.nitems) load_job(next, slot ^ 1);
+    __syncthreads();
+    if (next < b.nitems) {
+      prefetch(next, slot ^ 1);
+      cp_async_wait_group1();
+    } else {
+      cp_async_wait_all();
+    }
+    const PairJob& jb = s_job[slot];
+    int bx0, by0;
+    tile_of(jb, item, bx0, by0);
+    const int nbx = jb.nbx, nby = jb.nby;
+    uint32_t* const jwin = s_jwin[slot];
+    const uint32_t* const iwin = s_iw[slot];
+    const uint32_t* const ti0 = s_i0[slot];
+    const uint32_t* const ti1 = s_i1[slot];
 
     // ---- phase A: exhaustive search on the coarsest level --------------------
     {
-      const Plane I2 = jb.I[L - 1], J2 = jb.J[L - 1];
+      const Plane J2 = jb.J[L - 1];
       const int Xw0 = bx0 * kCoarseSide - R, Yw0 = by0 * kCoarseSide - R;
-      for (int idx = tid; idx < WROWS * WWORDS; idx += NT) {
-        const int wy = idx / WWORDS, wx = idx - wy * WWORDS;
-        const int y = clampi(Yw0 + wy, 0, J2.h - 1);
-        const int x = Xw0 + 4 * wx;
-        const uint8_t* row = J2.p + (size_t)y * J2.pitch;
-        uint32_t v;
-        if (x >= 0 && x + 3 <= J2.w - 1) v = __ldg(reinterpret_cast<const uint32_t*>(row + x));
-        else v = load4_clamped(row, x, J2.w);
-        s_jwin[wy][wx] = v;
-      }
-      for (int idx = tid; idx < TBY * kCoarseSide * TBX; idx += NT) {
-        const int ry = idx / TBX, wx = idx - ry * TBX;
-        uint32_t v = 0;
-        if (bx0 + wx < nbx && by0 + ry / kCoarseSide < nby)
-          v = __ldg(reinterpret_cast<const uint32_t*>(I2.p + (size_t)(by0 * kCoarseSide + ry) * I2.pitch +
-                                                      (bx0 + wx) * kCoarseSide));
-        s_iw[ry][wx] = v;
+      if (Xw0 < 0 || Yw0 < 0 || Xw0 + 4 * WWORDS > J2.w || Yw0 + WROWS > J2.h) {
+        // window words outside the coarsest level: clamp-to-edge
+        for (int c = tid; c < WROWS * WWORDS; c += NT) {
+          const int wy = c / WWORDS, wx = c - wy * WWORDS;
+          const int y = Yw0 + wy, x = Xw0 + 4 * wx;
+          if (!(y >= 0 && y < J2.h && x >= 0 && x + 3 <= J2.w - 1))
+            jwin[c] = load4_clamped(J2.p + (size_t)clampi(y, 0, J2.h - 1) * J2.pitch, x, J2.w);
+        }
       }
       for (int i = tid; i < NB; i += NT) s_best32[i] = 0xFFFFFFFFu;
       __syncthreads();
@@ -339,8 +380,8 @@ pair_kernel(const PairBatch b) {
       const int g = tid % G, bl = in_a ? tid / G : 0;
       const int bxl = bl % TBX, byl = bl / TBX;
       const bool active = in_a && (bx0 + bxl < nbx) && (by0 + byl < nby);
-      const uint32_t i0 = s_iw[byl * 4 + 0][bxl], i1 = s_iw[byl * 4 + 1][bxl];
-      const uint32_t i2 = s_iw[byl * 4 + 2][bxl], i3 = s_iw[byl * 4 + 3][bxl];
+      const uint32_t i0 = iwin[(byl * 4 + 0) * TBX + bxl], i1 = iwin[(byl * 4 + 1) * TBX + bxl];
+      const uint32_t i2 = iwin[(byl * 4 + 2) * TBX + bxl], i3 = iwin[(byl * 4 + 3) * TBX + bxl];
       const uint32_t lam18 = (uint32_t)lam << 18;
       // acc[j][c & 3] holds candidate c = dy - k (vy = c - R): it receives row k
       // of the block at window row dy, starts at k = 0 and completes at k = 3.
@@ -352,7 +393,7 @@ pair_kernel(const PairBatch b) {
 #pragma unroll
         for (int k = 0; k < 4; k++) acc[j][k] = 0;
       }
-      const uint32_t* wrow = &s_jwin[byl * 4][bxl + g];
+      const uint32_t* wrow = jwin + (byl * 4) * WWORDS + bxl + g;
 #pragma unroll
       for (int dy = 0; dy < 2 * R + 4; dy++) {
         const uint32_t wlo = wrow[dy * WWORDS], whi = wrow[dy * WWORDS + 1];
@@ -398,10 +439,8 @@ pair_kernel(const PairBatch b) {
 
     // ---- phase B: refinement at levels L-2 .. 0 -------------------------------
     if (fast) {
-      cp_async_wait_all();
-      __syncthreads();
-      refine_level<8, 2, NT, NB, TBX>(jb.J[1], s_i1, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_best32, s_win, tid);
-      refine_level<16, 2, NT, NB, TBX>(jb.J[0], s_i0, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_best32, s_win, tid);
+      refine_level<8, 2, NT, NB, TBX>(jb.J[1], ti1, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_best32, s_win, tid);
+      refine_level<16, 2, NT, NB, TBX>(jb.J[0], ti0, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_best32, s_win, tid);
     } else {
       for (int l = L - 2; l >= 0; l--) {
         const Plane Il = jb.I[l], Jl = jb.J[l];
@@ -476,7 +515,7 @@ pair_kernel(const PairBatch b) {
             if (nx == 16) {
               uint4 q;
               if (fast && bx - bx0 < TBX && bx == (x >> 4) && y - ys < TBY * 16 && by == (y >> 4))
-                q = *reinterpret_cast<const uint4*>(s_i0 + ((y - ys) * TBX + (bx - bx0)) * 4);
+                q = *reinterpret_cast<const uint4*>(ti0 + ((y - ys) * TBX + (bx - bx0)) * 4);
               else
                 q = __ldg(reinterpret_cast<const uint4*>(irow + x));
               iv[0] = q.x; iv[1] = q.y; iv[2] = q.z; iv[3] = q.w;
