@@ -92,6 +92,9 @@ typedef struct {
                                           0 = autotuned per resolution (0, 0) */
   int time_kernels;                    /* record CUDA events around every kernel launch (0) */
   int step_frames;                     /* server: frames copied per clip per step (0 = fill the window) (32) */
+  int kernel_mode;                     /* 0: split coarse / refine kernels on two streams for the default
+                                          estimator (levels 3, radius_refine 2), fused otherwise;
+                                          1: always the fused kernel (0) */
 } analyser_params;
 
 /* One measure of one pair, in the order of (kind, a, b). */

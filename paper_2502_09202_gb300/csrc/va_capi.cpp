@@ -108,6 +108,7 @@ int analyser_default_params(analyser_params* p) {
   p->tile_y = 0;
   p->time_kernels = 0;
   p->step_frames = 32;
+  p->kernel_mode = 0;
   return ANALYSER_OK;
 }
 

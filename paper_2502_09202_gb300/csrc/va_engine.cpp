@@ -67,6 +67,10 @@ int validate_params(const analyser_params& p, std::string& why) {
     why = "tile_x x tile_y is not a compiled tile shape";
     return ANALYSER_ERR_INVALID_ARG;
   }
+  if (p.kernel_mode < 0 || p.kernel_mode > 1) {
+    why = "kernel_mode must be 0 (split kernels for the default estimator) or 1 (fused kernel)";
+    return ANALYSER_ERR_INVALID_ARG;
+  }
   if (p.step_frames < 0) {
     why = "step_frames must be >= 0";
     return ANALYSER_ERR_INVALID_ARG;
@@ -124,6 +128,10 @@ Engine::~Engine() {
   for (cudaEvent_t& e : ev_)
     if (e) cudaEventDestroy(e);
   if (ev_up_) cudaEventDestroy(ev_up_);
+  if (ev_chunk_) cudaEventDestroy(ev_chunk_);
+  if (ev_join_) cudaEventDestroy(ev_join_);
+  if (rstream) cudaStreamDestroy(rstream);
+  if (d_cvec) cudaFree(d_cvec);
   if (cstream) cudaStreamDestroy(cstream);
   if (stream) cudaStreamDestroy(stream);
 }
@@ -152,6 +160,9 @@ int Engine::init(std::string& why) {
   VA_CUDA_TRY(cudaSetDevice(p.device), why);
   VA_CUDA_TRY(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking), why);
   VA_CUDA_TRY(cudaStreamCreateWithFlags(&cstream, cudaStreamNonBlocking), why);
+  VA_CUDA_TRY(cudaStreamCreateWithFlags(&rstream, cudaStreamNonBlocking), why);
+  VA_CUDA_TRY(cudaEventCreateWithFlags(&ev_chunk_, cudaEventDisableTiming), why);
+  VA_CUDA_TRY(cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming), why);
   VA_CUDA_TRY(cudaEventCreateWithFlags(&ev_up_, cudaEventDisableTiming), why);
   VA_CUDA_TRY(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, p.device), why);
   // Q(k) = floor(sqrt(k) * 2^16) for every k = vx^2 + vy^2 the search can produce
@@ -513,17 +524,39 @@ int Engine::wave_launch() {
     }
     cap_vec = vec_total;
   }
+  // groups of pairs sharing a tile shape; with the split kernels a group is
+  // also a chunk of the wave, so that chunk c's refinement runs beside chunk
+  // c+1's coarse search
+  const bool split = p.levels == 3 && p.radius_refine == 2 && p.kernel_mode == 0;
+  const int chunk = split ? std::max(4, (npairs + 3) / 4) : npairs + 1;
+  size_t cvec_total = 0;
+  for (auto& w : wp_) {
+    const Geometry& g = w.clip->geo;
+    const int h0 = key_kind(w.key) == kFrame ? g.H : g.H / 2;
+    cvec_total += (size_t)(g.W / g.B0) * (h0 / g.B0);
+  }
+  if (split && cvec_total > cap_cvec) {
+    if (d_cvec) cudaFree(d_cvec);
+    d_cvec = nullptr;
+    if (cudaMalloc(&d_cvec, sizeof(short2) * cvec_total) != cudaSuccess) {
+      status = ANALYSER_ERR_OOM; message = "cudaMalloc(coarse vectors)"; return status;
+    }
+    cap_cvec = cvec_total;
+  }
   struct Group { int first, count, items, tbx, tby; };
   std::vector<Group> groups;
   int items = 0;
+  size_t cvec_off = 0;
   for (int i = 0; i < npairs; i++) {
     WavePair& w = wp_[i];
-    if (groups.empty() || groups.back().tbx != w.tbx || groups.back().tby != w.tby) {
+    if (groups.empty() || groups.back().tbx != w.tbx || groups.back().tby != w.tby || groups.back().count >= chunk) {
       groups.push_back({i, 0, 0, w.tbx, w.tby});
       items = 0;
     }
     short2* vp = w.vec_off ? d_vec + (w.vec_off - 1) : nullptr;
     const int n = setup_pair_job(*w.clip, w.key, h_pjobs[i], items, d_rec + (size_t)kRecWords * i, vp);
+    h_pjobs[i].cvec = split ? d_cvec + cvec_off : nullptr;
+    cvec_off += (size_t)h_pjobs[i].nbx * h_pjobs[i].nby;
     items += n;
     groups.back().count++;
     groups.back().items = items;
@@ -582,15 +615,30 @@ int Engine::wave_launch() {
     b.qmax = qmax;
     b.cfg = {p.levels, p.radius_coarse, p.radius_refine, p.mv_cost};
     b.status = d_status;
-    const int nt = pair_threads(p.radius_coarse, gr.tbx, gr.tby);
-    int per_sm = 1;
-    (void)nt;
-    per_sm = pair_blocks_per_sm(p.radius_coarse, gr.tbx, gr.tby);
-    const int grid = std::max(1, std::min(gr.items, sm_count * std::max(per_sm, 1)));
-    e = launch_pairs(b, gr.tbx, gr.tby, grid, stream);
-    if (e) return fail(e, "pair_kernel");
-    n_launches++;
-    n_pair_launches++;
+    if (split) {
+      // coarse search on the main stream, refinement + sums on the second one
+      e = launch_coarse(b, gr.tbx, gr.tby, stream);
+      if (e) return fail(e, "coarse_kernel");
+      e = cudaEventRecord(ev_chunk_, stream);
+      if (!e) e = cudaStreamWaitEvent(rstream, ev_chunk_, 0);
+      if (e) return fail(e, "cudaStreamWaitEvent(chunk)");
+      e = launch_refine(b, gr.tbx, gr.tby, rstream);
+      if (e) return fail(e, "refine_kernel");
+      n_launches += 2;
+      n_pair_launches += 2;
+    } else {
+      const int per_sm = pair_blocks_per_sm(p.radius_coarse, gr.tbx, gr.tby);
+      const int grid = std::max(1, std::min(gr.items, sm_count * std::max(per_sm, 1)));
+      e = launch_pairs(b, gr.tbx, gr.tby, grid, stream);
+      if (e) return fail(e, "pair_kernel");
+      n_launches++;
+      n_pair_launches++;
+    }
+  }
+  if (split && !groups.empty()) {
+    e = cudaEventRecord(ev_join_, rstream);
+    if (!e) e = cudaStreamWaitEvent(stream, ev_join_, 0);
+    if (e) return fail(e, "cudaStreamWaitEvent(join)");
   }
   if (timed && !groups.empty()) cudaEventRecord(ev_[3], stream);
   if (npairs) {

@@ -144,6 +144,10 @@ class Engine {
   int* h_status = nullptr;
   cudaEvent_t ev_[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t ev_up_ = nullptr;     // last frame copy
+  cudaStream_t rstream = nullptr;   // refinement kernels of the split path
+  cudaEvent_t ev_chunk_ = nullptr, ev_join_ = nullptr;
+  short2* d_cvec = nullptr;         // coarse vectors between the split kernels
+  size_t cap_cvec = 0;
   bool up_pending_ = false;
   // wave in flight (between wave_launch and wave_complete)
   bool inflight_ = false;

@@ -32,6 +32,7 @@ struct PairJob {
   int item_begin;            // index of this job's first tile in the batch
   unsigned long long* rec;   // kRecWords accumulators (zeroed before the launch)
   short2* vec;               // optional level-0 motion field dump (nby*nbx), or null
+  short2* cvec;              // coarse vectors (nby*nbx) between the split kernels, or null
 };
 
 struct SearchCfg {
@@ -58,5 +59,10 @@ cudaError_t launch_pairs(const PairBatch& b, int tbx, int tby, int grid, cudaStr
 bool pair_tile_supported(int radius, int tbx, int tby);
 int pair_threads(int radius, int tbx, int tby);
 int pair_blocks_per_sm(int radius, int tbx, int tby);
+// the default estimator as two kernels (va_split.cu): coarse search, then
+// refinement + sums; each launch runs one CTA per (pair, tile)
+bool split_applies(const PairBatch& b);
+cudaError_t launch_coarse(const PairBatch& b, int tbx, int tby, cudaStream_t st);
+cudaError_t launch_refine(const PairBatch& b, int tbx, int tby, cudaStream_t st);
 
 }  // namespace va

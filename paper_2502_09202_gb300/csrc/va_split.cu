@@ -1,0 +1,161 @@
+// The default estimator (3 pyramid levels, level-0 blocks of 16, refinement
+// radius 2) as two kernels that the engine pipelines over chunks of a wave on
+// two streams, so that the ALU-bound coarse search of one chunk runs beside the
+// latency-bound refinement and correlation sums of the previous one:
+//   coarse_kernel  one CTA per (pair, tile): exhaustive coarse search, vectors
+//                  written to the pair's coarse-vector array;
+//   refine_kernel  one CTA per (pair, tile): both refinement levels, the AMM
+//                  term and the motion-compensated sums.
+// Arithmetic and candidate order are those of the fused pair kernel.
+#include "va_device.cuh"
+
+namespace va {
+namespace {
+
+template <int R, int TBX, int TBY>
+struct CoarseShape {
+  static constexpr int G = (2 * R + 4) / 4;
+  static constexpr int NB = TBX * TBY;
+  static constexpr int NT = (NB * G + 31) / 32 * 32;
+  static constexpr int WROWS = TBY * kCoarseSide + 2 * R;
+  static constexpr int WWORDS = TBX + G;
+};
+
+template <int TBX, int TBY>
+struct RefineShape {
+  static constexpr int NB = TBX * TBY;
+  static constexpr int NT = NB * 4 < 64 ? 64 : NB * 4;   // one level-0 task (block, column) per thread
+};
+
+__device__ __forceinline__ int find_job(const PairBatch& b, int item) {
+  int lo = 0, hi = b.njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (b.jobs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int NT>
+__device__ __forceinline__ void copy_job(const PairBatch& b, int item, PairJob* dst, int tid) {
+  const int* src = reinterpret_cast<const int*>(b.jobs + find_job(b, item));
+  for (int i = tid; i < (int)(sizeof(PairJob) / 4); i += NT) reinterpret_cast<int*>(dst)[i] = src[i];
+}
+
+template <int R, int TBX, int TBY>
+__global__ void __launch_bounds__(CoarseShape<R, TBX, TBY>::NT) coarse_kernel(const PairBatch b) {
+  using S = CoarseShape<R, TBX, TBY>;
+  constexpr int NB = S::NB, NT = S::NT, WROWS = S::WROWS, WWORDS = S::WWORDS;
+  __shared__ uint32_t s_jwin[WROWS * WWORDS];
+  __shared__ uint32_t s_iw[TBY * kCoarseSide * TBX];
+  __shared__ uint32_t s_best32[NB];
+  __shared__ int s_vx[NB], s_vy[NB];
+  __shared__ PairJob s_job;
+  const int tid = threadIdx.x, item = blockIdx.x;
+  copy_job<NT>(b, item, &s_job, tid);
+  __syncthreads();
+  const PairJob& jb = s_job;
+  const int local = item - jb.item_begin;
+  const int bx0 = (local % jb.tiles_x) * TBX, by0 = (local / jb.tiles_x) * TBY;
+  const int nbx = jb.nbx, nby = jb.nby;
+  const Plane J2 = jb.J[2], I2 = jb.I[2];
+  const int Xw0 = bx0 * kCoarseSide - R, Yw0 = by0 * kCoarseSide - R;
+  for (int c = tid; c < WROWS * WWORDS; c += NT) {
+    const int wy = c / WWORDS, wx = c - wy * WWORDS;
+    const int y = clampi(Yw0 + wy, 0, J2.h - 1), x = Xw0 + 4 * wx;
+    const uint8_t* row = J2.p + (size_t)y * J2.pitch;
+    s_jwin[c] = (x >= 0 && x + 3 <= J2.w - 1) ? __ldg(reinterpret_cast<const uint32_t*>(row + x))
+                                              : load4_clamped(row, x, J2.w);
+  }
+  for (int c = tid; c < TBY * kCoarseSide * TBX; c += NT) {
+    const int r = c / TBX, k = c - r * TBX;
+    s_iw[c] = (bx0 + k < nbx && by0 + r / kCoarseSide < nby)
+                  ? __ldg(reinterpret_cast<const uint32_t*>(I2.p + (size_t)(by0 * kCoarseSide + r) * I2.pitch +
+                                                            (bx0 + k) * kCoarseSide))
+                  : 0u;
+  }
+  for (int i = tid; i < NB; i += NT) s_best32[i] = 0xFFFFFFFFu;
+  __syncthreads();
+  coarse_phase<R, TBX, TBY, NT>(s_jwin, s_iw, bx0, by0, nbx, nby, b.cfg.lambda, s_best32, s_vx, s_vy, tid);
+  for (int i = tid; i < NB; i += NT) {
+    const int bx = bx0 + i % TBX, by = by0 + i / TBX;
+    if (bx < nbx && by < nby) jb.cvec[(size_t)by * nbx + bx] = make_short2((short)s_vx[i], (short)s_vy[i]);
+  }
+}
+
+template <int TBX, int TBY>
+__global__ void __launch_bounds__(RefineShape<TBX, TBY>::NT) refine_kernel(const PairBatch b) {
+  using S = RefineShape<TBX, TBY>;
+  constexpr int NB = S::NB, NT = S::NT;
+  __shared__ __align__(16) uint32_t s_i0[TBY * 16 * TBX * 4];
+  __shared__ __align__(16) uint32_t s_i1[TBY * 8 * TBX * 2];
+  __shared__ uint32_t s_win[NB * 20 * 6];
+  __shared__ uint32_t s_best32[NB];
+  __shared__ int s_vx[NB], s_vy[NB];
+  __shared__ unsigned long long s_red[NT / 32][kRecWords];
+  __shared__ PairJob s_job;
+  const int tid = threadIdx.x, item = blockIdx.x;
+  copy_job<NT>(b, item, &s_job, tid);
+  __syncthreads();
+  const PairJob& jb = s_job;
+  const int local = item - jb.item_begin;
+  const int bx0 = (local % jb.tiles_x) * TBX, by0 = (local / jb.tiles_x) * TBY;
+  const int nbx = jb.nbx, nby = jb.nby;
+  for (int c = tid; c < TBY * 16 * TBX; c += NT) {
+    const int r = c / TBX, k = c - r * TBX;
+    if (bx0 + k < nbx && by0 + r / 16 < nby)
+      cp_async16(&s_i0[c * 4], jb.I[0].p + (size_t)(by0 * 16 + r) * jb.I[0].pitch + (bx0 + k) * 16);
+  }
+  for (int c = tid; c < TBY * 8 * TBX; c += NT) {
+    const int r = c / TBX, k = c - r * TBX;
+    if (bx0 + k < nbx && by0 + r / 8 < nby)
+      cp_async8(&s_i1[c * 2], jb.I[1].p + (size_t)(by0 * 8 + r) * jb.I[1].pitch + (bx0 + k) * 8);
+  }
+  cp_async_commit();
+  for (int i = tid; i < NB; i += NT) {
+    const int bx = bx0 + i % TBX, by = by0 + i / TBX;
+    short2 v = make_short2(0, 0);
+    if (bx < nbx && by < nby) v = jb.cvec[(size_t)by * nbx + bx];
+    s_vx[i] = v.x;
+    s_vy[i] = v.y;
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int lam = b.cfg.lambda;
+  refine_level<8, 2, NT, NB, TBX>(jb.J[1], s_i1, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_best32, s_win, tid);
+  refine_level<16, 2, NT, NB, TBX>(jb.J[0], s_i0, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_best32, s_win, tid);
+  sums_phase<TBX, TBY, NT>(b, jb, bx0, by0, 16, true, s_i0, s_vx, s_vy, s_red, tid);
+}
+
+}  // namespace
+
+#define VA_SPLIT_TILES(X, R) X(R, 8, 4) X(R, 4, 4) X(R, 8, 2) X(R, 16, 2) X(R, 4, 8)
+#define VA_SPLIT_RADII(X) VA_SPLIT_TILES(X, 8) VA_SPLIT_TILES(X, 16) VA_SPLIT_TILES(X, 24)
+
+bool split_applies(const PairBatch& b) { return b.cfg.levels == 3 && b.cfg.refine == 2; }
+
+cudaError_t launch_coarse(const PairBatch& b, int tbx, int tby, cudaStream_t st) {
+  if (b.nitems <= 0) return cudaSuccess;
+#define VA_CASE(R_, X_, Y_)                                                                  \
+  if (b.cfg.radius == R_ && tbx == X_ && tby == Y_) {                                        \
+    coarse_kernel<R_, X_, Y_><<<b.nitems, CoarseShape<R_, X_, Y_>::NT, 0, st>>>(b);          \
+    return cudaGetLastError();                                                               \
+  }
+  VA_SPLIT_RADII(VA_CASE)
+#undef VA_CASE
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_refine(const PairBatch& b, int tbx, int tby, cudaStream_t st) {
+  if (b.nitems <= 0) return cudaSuccess;
+#define VA_CASE(X_, Y_)                                                              \
+  if (tbx == X_ && tby == Y_) {                                                      \
+    refine_kernel<X_, Y_><<<b.nitems, RefineShape<X_, Y_>::NT, 0, st>>>(b);          \
+    return cudaGetLastError();                                                       \
+  }
+  VA_CASE(8, 4) VA_CASE(4, 4) VA_CASE(8, 2) VA_CASE(16, 2) VA_CASE(4, 8)
+#undef VA_CASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace va

@@ -32,7 +32,7 @@ class Params(ctypes.Structure):
         ("kf_theta", c_double),
         ("device", c_int), ("window_frames", c_int), ("mem_budget_bytes", c_ull), ("want_motion", c_int),
         ("tile_x", c_int), ("tile_y", c_int), ("time_kernels", c_int),
-        ("step_frames", c_int),
+        ("step_frames", c_int), ("kernel_mode", c_int),
     ]
 
 

@@ -214,3 +214,26 @@ def test_long_clip_streams_through_a_small_window():
                 s += c
             a.finish()
             _compare_results(a.results(), ref)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_split_and_fused_kernels_match_the_oracle(mode):
+    """kernel_mode 0 runs the coarse and refinement kernels on two streams,
+    kernel_mode 1 the fused kernel: both must equal the oracle."""
+    api = _api()
+    w, h = 333, 190
+    clip = synth.Clip(synth.ClipSpec(w, h, 5, 25.0, synth.BFF, 9, 3.0,
+                                     synth.SceneStyle(n_objects=(4, 6), obj_speed=10, cell=8, bg_kind="textured")))
+    frames = clip.frames()
+    kinds, ia, ib = [0, 1, 2, 0, 0, 1], [0, 1, 2, 3, 4, 4], [1, 2, 3, 4, 0, 4]
+    rec, mot = api.measure_pairs(_dev(frames), kinds, ia, ib, want_motion=True, kernel_mode=mode)
+    for k in range(len(kinds)):
+        ref, vec = _oracle_pair(kinds[k], frames[ia[k]], frames[ib[k]])
+        assert list(rec[k]) == [ref[f] for f in REC7]
+        assert np.array_equal(mot[k], vec)
+    spec = synth.config_small()
+    frames = synth.Clip(spec).frames()
+    with api.Analyser(spec.width, spec.height, spec.fps, kernel_mode=mode) as a:
+        a.push(frames)
+        a.finish()
+        _compare_results(a.results(), OA.analyse_frames(frames))
