@@ -55,131 +55,164 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_group1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Shared-memory window of one block at a refinement level of block side S
+// (radius 2): WR rows of RW words copied from the 4-byte boundary at or before
+// the window's first byte (candidate dx = -2).  Every block owns one region of
+// kRefineWinWords words that both levels use, so a block's four lanes never
+// touch another block's window and the levels need no CTA barrier; the stride
+// (28 banks) puts the words the level-0 lanes read together on 32 distinct
+// banks (level 1: at most two-way).
+constexpr int kRefineWinWords = 124;
+template <int S>
+struct RefineWin;
+template <>
+struct RefineWin<16> {
+  static constexpr int WR = 20, RW = 6, H = 1;
+};
+template <>
+struct RefineWin<8> {
+  static constexpr int WR = 12, RW = 4, H = 2;
+};
+
 // Refinement of every block of a tile at one pyramid level (block side S,
-// radius RR), candidates v = 2*parent + d, |d| <= RR.
-//  - each block's (S+2RR)-row search window in J is staged in shared memory
-//    (clamp-to-edge);
-//  - a thread owns one (block, dx, 4-pixel column q) with that I column in
-//    registers (read from the tile staged in s_i) and slides down the window
-//    rows, feeding the 2RR+1 dy candidates; the S/4 column partials are summed
-//    with xor shuffles;
-//  - a candidate's key is (cost << 8) | t with cost = SAD + lambda*|v|_1 and
-//    t = (|v|_1 - min|v|_1)*25 + dy_i*5 + dx_i, which orders the block's 25
-//    candidates exactly as (cost, |v|_1, vy, vx); the minimum goes to s_best.
-// Afterwards s_vx/s_vy hold the level-l vectors.
-template <int S, int RR, int NT, int NB, int TBX>
+// radius RR), candidates v = 2*parent + d, |d| <= RR (Sec. III.A, coarse to
+// fine block matching).  Four lanes own a block (lanes 4*bl .. 4*bl+3):
+//  - they copy the block's window of J into shared memory (cp.async, rows
+//    t, t+4, ...; clamp-to-edge loads where the window leaves the image
+//    horizontally, row indices clamped), so a level needs no CTA barrier;
+//  - lane t covers 4-pixel column t % (S/4) and row slice t / (S/4) of the
+//    block, keeps those I words in registers and slides down the window rows,
+//    feeding all 25 (dx, dy) candidates; the four partial sums are added with
+//    xor shuffles;
+//  - a candidate's key is (cost << 8) + rank with cost = SAD + lambda*|v|_1 and
+//    rank = (|v|_1 - min|v|_1)*25 + dy_i*5 + dx_i, which orders the block's 25
+//    candidates exactly as (cost, |v|_1, vy, vx).
+// Afterwards s_vx/s_vy hold the level-l vectors (visible to the block's own
+// lanes; other threads need a CTA barrier first).  With SUMS the four lanes
+// then add the motion-compensated sums of their pixels (I column in registers,
+// warped J from the window) to part[] =
+// {sum I, sum J, sum I^2, sum J^2, sum IJ, sum |I-J|}.
+template <int S, int RR, int NT, int NB, int TBX, bool SUMS>
 __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i, int bx0, int by0, int nbx, int nby,
-                                             int lam, int* s_vx, int* s_vy, uint32_t* s_best, uint32_t* s_win,
+                                             int lam, int* s_vx, int* s_vy, uint32_t* s_win, uint32_t (&part)[6],
                                              int tid) {
-  static_assert(RR == 2, "relative candidate ranks assume radius 2");
-  constexpr int NQ = S / 4, ND = 2 * RR + 1;
-  constexpr int WR = S + 2 * RR, WW = (S + 2 * RR + 2) / 4 + 1;
-  constexpr int IW = TBX * NQ;     // words per row of the staged I tile
-  for (int task = tid; task < NB * WR; task += NT) {
-    const int bl = task / WR, w = task - bl * WR;
-    const int bx = bx0 + bl % TBX, by = by0 + bl / TBX;
-    uint32_t* dst = s_win + task * WW;
-    if (bx < nbx && by < nby) {
-      const int xs = (bx * S + 2 * s_vx[bl] - RR) & ~3;
-      const int yy = clampi(by * S + 2 * s_vy[bl] - RR + w, 0, Jl.h - 1);
-      const uint8_t* row = Jl.p + (size_t)yy * Jl.pitch;
-      if (xs >= 0 && xs + 4 * WW <= Jl.w) {
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(row + xs);
+  static_assert(RR == 2, "candidate ranks and window shapes assume radius 2");
+  using Wn = RefineWin<S>;
+  constexpr int NQ = S / 4, H = Wn::H, RT = S / H;   // column lanes, row slices, rows per slice
+  constexpr int IW = TBX * NQ;                       // words per row of the staged I tile
+  static_assert(NQ * H == 4 && Wn::WR % 4 == 0, "four lanes per block");
+  static_assert(NT % 32 == 0 && NT >= NB * 4 && (NB * 4) % 32 == 0, "one task per thread, whole warps");
+  if ((tid & ~31) >= NB * 4) return;   // warps without a block (warp-uniform)
+  const int bl = tid >> 2, t = tid & 3;
+  const int q = t % NQ, h = t / NQ;
+  const int bxl = bl % TBX, byl = bl / TBX;
+  const bool valid = bx0 + bxl < nbx && by0 + byl < nby;
+  const int cx = 2 * s_vx[bl], cy = 2 * s_vy[bl];
+  const int xw = (bx0 + bxl) * S + cx - RR;   // image position of candidate (-RR, -RR)
+  const int yw = (by0 + byl) * S + cy - RR;
+  const int xa = xw & ~3, s8 = 8 * (xw & 3);
+  static_assert(Wn::WR * Wn::RW <= kRefineWinWords, "window fits the block's region");
+  uint32_t* const win = s_win + bl * kRefineWinWords;
+
+  // ---- staging ----------------------------------------------------------------
+  if (valid) {
+    const bool inside = xa >= 0 && xa + 4 * Wn::RW <= Jl.w;
 #pragma unroll
-        for (int k = 0; k < WW; k++) dst[k] = __ldg(src + k);
+    for (int k = 0; k < Wn::WR / 4; k++) {
+      const int r = t + 4 * k;
+      const uint8_t* row = Jl.p + (size_t)clampi(yw + r, 0, Jl.h - 1) * Jl.pitch;
+      if (inside) {
+#pragma unroll
+        for (int c = 0; c < Wn::RW; c++) cp_async4(win + r * Wn::RW + c, row + xa + 4 * c);
       } else {
 #pragma unroll
-        for (int k = 0; k < WW; k++) dst[k] = load4_clamped(row, xs + 4 * k, Jl.w);
+        for (int c = 0; c < Wn::RW; c++) win[r * Wn::RW + c] = load4_clamped(row, xa + 4 * c, Jl.w);
       }
     }
   }
-  for (int i = tid; i < NB; i += NT) s_best[i] = 0xFFFFFFFFu;
-  __syncthreads();
-  // task = (block, 4-pixel column q): all ND x ND candidates of that column
-  for (int base = 0; base < NB * NQ; base += NT) {
-    const int it = base + tid;
-    const int bl = it / NQ, q = it - bl * NQ;
-    const int bxl = bl % TBX, byl = bl / TBX;
-    const bool valid = it < NB * NQ && bx0 + bxl < nbx && by0 + byl < nby;
-    uint32_t acc[ND][ND];     // [dx][dy]
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncwarp();
+
+  // ---- candidates -------------------------------------------------------------
+  uint32_t acc[5][5];   // [dx][dy]
 #pragma unroll
-    for (int a = 0; a < ND; a++)
+  for (int a = 0; a < 5; a++)
 #pragma unroll
-      for (int d = 0; d < ND; d++) acc[a][d] = 0;
-    int cx = 0, cy = 0;
+    for (int d = 0; d < 5; d++) acc[a][d] = 0;
+  if (valid) {
+    uint32_t icol[RT];
+    const uint32_t* ip = s_i + (byl * S + h * RT) * IW + bxl * NQ + q;
+#pragma unroll
+    for (int i = 0; i < RT; i++) icol[i] = ip[i * IW];
+    const uint32_t* wp = win + (h * RT) * Wn::RW + q;
+#pragma unroll
+    for (int w = 0; w < RT + 2 * RR; w++) {
+      const uint32_t w0 = wp[w * Wn::RW], w1 = wp[w * Wn::RW + 1], w2 = wp[w * Wn::RW + 2];
+      const uint32_t u0 = __funnelshift_r(w0, w1, s8), u1 = __funnelshift_r(w1, w2, s8);
+      const uint32_t jw[5] = {u0, __funnelshift_r(u0, u1, 8), __funnelshift_r(u0, u1, 16),
+                              __funnelshift_r(u0, u1, 24), u1};
+#pragma unroll
+      for (int d = 0; d < 5; d++) {
+        const int i = w - d;
+        if (i >= 0 && i < RT) {
+#pragma unroll
+          for (int a = 0; a < 5; a++) acc[a][d] = sad4(icol[i], jw[a], acc[a][d]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 1; off <= 2; off <<= 1) {
+#pragma unroll
+    for (int a = 0; a < 5; a++)
+#pragma unroll
+      for (int d = 0; d < 5; d++) acc[a][d] += __shfl_xor_sync(0xFFFFFFFFu, acc[a][d], off);
+  }
+  uint32_t best = 0xFFFFFFFFu;
+  if (valid) {
+    // key = acc*256 + |v|_1*(256*lambda + 25) + 5*dy_i + dx_i - 25*min|v|_1,
+    // split into a dx part and a dy part (exact in 32 bits: key < 2^25)
+    const int n1min = max(abs(cx) - RR, 0) + max(abs(cy) - RR, 0);
+    const uint32_t k1 = (uint32_t)lam * 256u + 25u;
+    uint32_t kx[5], ky[5];
+#pragma unroll
+    for (int a = 0; a < 5; a++) kx[a] = (uint32_t)abs(cx + a - RR) * k1 + (uint32_t)a - 25u * (uint32_t)n1min;
+#pragma unroll
+    for (int d = 0; d < 5; d++) ky[d] = (uint32_t)abs(cy + d - RR) * k1 + 5u * (uint32_t)d;
+#pragma unroll
+    for (int d = 0; d < 5; d++)
+#pragma unroll
+      for (int a = 0; a < 5; a++) best = min(best, acc[a][d] * 256u + kx[a] + ky[d]);
+  }
+  const int r = (int)(best & 255u) % 25;
+  if (valid && t == 0) {
+    s_vx[bl] = cx + r % 5 - RR;
+    s_vy[bl] = cy + r / 5 - RR;
+  }
+  if constexpr (SUMS) {
     if (valid) {
-      cx = 2 * s_vx[bl];
-      cy = 2 * s_vy[bl];
-      uint32_t icol[S];
-      const uint32_t* ip = s_i + (byl * S) * IW + bxl * NQ + q;
+      // pixel (4q + c, i) of the block meets window byte (xw & 3) + 4q + c + dx_i of row i + dy_i
+      const int o = (xw & 3) + r % 5, dyi = r / 5, sh = 8 * (o & 3);
+      const uint32_t* ip = s_i + (byl * S + h * RT) * IW + bxl * NQ + q;
+      const uint32_t* jp = win + (h * RT + dyi) * Wn::RW + q + (o >> 2);
+      uint32_t si = 0, sj = 0, sii = 0, sjj = 0, sij = 0, sab = 0;
 #pragma unroll
-      for (int i = 0; i < S; i++) icol[i] = ip[i * IW];
-      const int xstart = (bx0 + bxl) * S + cx - RR;
-      const int o = (xstart - (xstart & ~3)) + 4 * q;    // byte offset of dx = 0 in the window row
-      const int wo = o >> 2, sh = (o & 3) * 8;
-      const uint32_t* wp = s_win + bl * (WR * WW) + wo;
-#pragma unroll
-      for (int w = 0; w < WR; w++) {
-        const uint32_t w0 = wp[w * WW], w1 = wp[w * WW + 1], w2 = wp[w * WW + 2];
-        // the 5 dx alignments come from 3 consecutive words
-        const uint64_t lo = ((uint64_t)w1 << 32) | w0;
-        const uint64_t hi = ((uint64_t)w2 << 32) | w1;
-        uint32_t jw[ND];
-#pragma unroll
-        for (int a = 0; a < ND; a++) {
-          // byte offset o&3 + a within w0..w2
-          const int bo = a;   // added to the runtime shift below
-          jw[a] = (sh + 8 * bo < 32) ? (uint32_t)(lo >> (sh + 8 * bo)) : (uint32_t)(hi >> (sh + 8 * bo - 32));
-        }
-#pragma unroll
-        for (int d = 0; d < ND; d++) {
-          const int i = w - d;
-          if (i >= 0 && i < S) {
-#pragma unroll
-            for (int a = 0; a < ND; a++) acc[a][d] = sad4(icol[i], jw[a], acc[a][d]);
-          }
-        }
+      for (int i = 0; i < RT; i++) {
+        const uint32_t iv = ip[i * IW];
+        const uint32_t w0 = jp[i * Wn::RW], w1 = sh ? jp[i * Wn::RW + 1] : 0u;
+        const uint32_t jv = __funnelshift_r(w0, w1, sh);
+        si = __dp4a(iv, 0x01010101u, si);
+        sj = __dp4a(jv, 0x01010101u, sj);
+        sii = __dp4a(iv, iv, sii);
+        sjj = __dp4a(jv, jv, sjj);
+        sij = __dp4a(iv, jv, sij);
+        sab = sad4(iv, jv, sab);
       }
-    }
-#pragma unroll
-    for (int off = NQ / 2; off >= 1; off >>= 1) {
-#pragma unroll
-      for (int a = 0; a < ND; a++)
-#pragma unroll
-        for (int d = 0; d < ND; d++) acc[a][d] += __shfl_xor_sync(0xFFFFFFFFu, acc[a][d], off);
-    }
-    // every column lane holds all sums: lane q finalises the dy rows d = q (mod NQ)
-    uint32_t best = 0xFFFFFFFFu;
-    if (valid) {
-      const int n1min = max(abs(cx) - RR, 0) + max(abs(cy) - RR, 0);
-#pragma unroll
-      for (int d = 0; d < ND; d++) {
-        if (d % NQ == q) {
-          const int avy = abs(cy + d - RR);
-#pragma unroll
-          for (int a = 0; a < ND; a++) {
-            const int n1 = abs(cx + a - RR) + avy;
-            const uint32_t cost = acc[a][d] + (uint32_t)(lam * n1);
-            const uint32_t t = (uint32_t)((n1 - n1min) * 25 + d * 5 + a);
-            best = min(best, (cost << 8) | t);
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int off = NQ / 2; off >= 1; off >>= 1) best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, off));
-    if (valid && q == 0) atomicMin(&s_best[bl], best);
-  }
-  __syncthreads();
-  for (int i = tid; i < NB; i += NT) {
-    const uint32_t k = s_best[i];
-    if (k != 0xFFFFFFFFu) {
-      const int t = (int)(k & 255u) % 25;
-      s_vx[i] = 2 * s_vx[i] + (t % 5) - RR;
-      s_vy[i] = 2 * s_vy[i] + (t / 5) - RR;
+      part[0] += si; part[1] += sj; part[2] += sii; part[3] += sjj; part[4] += sij; part[5] += sab;
     }
   }
-  __syncthreads();
+  __syncwarp();   // the next level's lanes read s_vx/s_vy and rewrite the window
 }
 
 // Exhaustive search of every block of a tile on the coarsest level (block
@@ -253,14 +286,17 @@ __device__ __forceinline__ void coarse_phase(const uint32_t* jwin, const uint32_
   __syncthreads();
 }
 
-// Motion-compensated sums over the tile's pixels (the blocks' pixels and, for
-// edge tiles, the border strips beyond the block grid, which use the nearest
-// block's vector), the AMM term of every block, the optional motion dump, and
-// the CTA reduction into the pair's accumulators.  Level-0 I rows come from the
-// staged tile when `fast` (default estimator), otherwise from global memory.
+// Phase C of a tile (Sec. III.A, SWR and AMM): the integer sums of the
+// motion-compensated pair over the tile's pixels (a pixel outside the full
+// blocks takes the vector of the nearest block), the AMM term of every block,
+// the optional motion dump, and the CTA reduction into the pair's accumulators.
+// On the fast path part[] already holds each thread's share of the full-block
+// pixels (added during the level-0 refinement) and only the strips beyond the
+// last full block column/row are read here; otherwise every pixel of the tile
+// is read here.
 template <int TBX, int TBY, int NT>
 __device__ __forceinline__ void sums_phase(const PairBatch& b, const PairJob& jb, int bx0, int by0, int B0, bool fast,
-                                           const uint32_t* ti0, const int* s_vx, const int* s_vy,
+                                           const uint32_t (&part)[6], const int* s_vx, const int* s_vy,
                                            unsigned long long (*s_red)[kRecWords], int tid) {
   constexpr int NB = TBX * TBY, NW = NT / 32;
   const int nbx = jb.nbx, nby = jb.nby;
@@ -270,76 +306,14 @@ __device__ __forceinline__ void sums_phase(const PairBatch& b, const PairJob& jb
   const int xe = (bx0 + TBX >= nbx) ? W : (bx0 + TBX) * B0;
   const int ye = (by0 + TBY >= nby) ? H : (by0 + TBY) * B0;
   const int lim_w = min(J0.w, J0.pitch);
-  uint32_t si = 0, sj = 0, sii = 0, sjj = 0, sij = 0, sab = 0;
-  if (B0 == 16) {
-    // columns of 16 pixels: TBX block columns plus a possible ragged strip
-    constexpr int NCOL = TBX + 1, NGRP = NT / NCOL;
-    const int col = tid % NCOL, grp = tid / NCOL;
-    const int x = xs + 16 * col;
-    if (grp < NGRP && x < xe) {
-      const int bx = min(x >> 4, nbx - 1);
-      const int nx = min(16, xe - x);          // pixels of this column (16 except a ragged edge)
-      for (int y = ys + grp; y < ye; y += NGRP) {
-        const int by = min(y >> 4, nby - 1);
-        const int bl = (by - by0) * TBX + (bx - bx0);
-        const int vx = s_vx[bl], vy = s_vy[bl];
-        const uint8_t* irow = I0.p + (size_t)y * I0.pitch;
-        const uint8_t* jrow = J0.p + (size_t)clampi(y + vy, 0, H - 1) * J0.pitch;
-        const int xj = x + vx;
-        uint32_t iv[4], jv[4];
-        if (nx == 16) {
-          uint4 q;
-          if (fast && bx - bx0 < TBX && bx == (x >> 4) && y - ys < TBY * 16 && by == (y >> 4))
-            q = *reinterpret_cast<const uint4*>(ti0 + ((y - ys) * TBX + (bx - bx0)) * 4);
-          else
-            q = __ldg(reinterpret_cast<const uint4*>(irow + x));
-          iv[0] = q.x; iv[1] = q.y; iv[2] = q.z; iv[3] = q.w;
-          if (xj >= 0 && xj + 19 <= lim_w - 1) {
-            const uint32_t* p = reinterpret_cast<const uint32_t*>(jrow + (xj & ~3));
-            const uint32_t a0 = __ldg(p), a1 = __ldg(p + 1), a2 = __ldg(p + 2), a3 = __ldg(p + 3), a4 = __ldg(p + 4);
-            const int sh = 8 * (xj & 3);
-            jv[0] = __funnelshift_r(a0, a1, sh);
-            jv[1] = __funnelshift_r(a1, a2, sh);
-            jv[2] = __funnelshift_r(a2, a3, sh);
-            jv[3] = __funnelshift_r(a3, a4, sh);
-          } else {
-#pragma unroll
-            for (int k = 0; k < 4; k++) jv[k] = load4_clamped(jrow, xj + 4 * k, W);
-          }
-        } else {
-          // ragged right edge: bytes beyond W contribute zero to every sum
-#pragma unroll
-          for (int kw = 0; kw < 4; kw++) {
-            uint32_t a = 0, c = 0;
-#pragma unroll
-            for (int kb = 0; kb < 4; kb++) {
-              const int k = 4 * kw + kb;
-              if (k < nx) {
-                a |= (uint32_t)irow[x + k] << (8 * kb);
-                c |= (uint32_t)jrow[clampi(xj + k, 0, W - 1)] << (8 * kb);
-              }
-            }
-            iv[kw] = a;
-            jv[kw] = c;
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-          si = __dp4a(iv[k], 0x01010101u, si);
-          sj = __dp4a(jv[k], 0x01010101u, sj);
-          sii = __dp4a(iv[k], iv[k], sii);
-          sjj = __dp4a(jv[k], jv[k], sjj);
-          sij = __dp4a(iv[k], jv[k], sij);
-          sab = sad4(iv[k], jv[k], sab);
-        }
-      }
-    }
-  } else {
-    const int nwx = (xe - xs + 3) >> 2;
-    const int nrows = ye - ys;
+  uint32_t si = part[0], sj = part[1], sii = part[2], sjj = part[3], sij = part[4], sab = part[5];
+  // pixels of [x0, x1) x [y0, y1), 4-pixel words from x0 (a multiple of 4)
+  auto region = [&](int x0, int x1, int y0, int y1) {
+    const int nwx = (x1 - x0 + 3) >> 2;
+    const int nrows = y1 - y0;
     for (int idx = tid; idx < nrows * nwx; idx += NT) {
       const int ry = idx / nwx, wx = idx - ry * nwx;
-      const int y = ys + ry, x = xs + 4 * wx;
+      const int y = y0 + ry, x = x0 + 4 * wx;
       const int bx = min(x / B0, nbx - 1), by = min(y / B0, nby - 1);
       const int bl = (by - by0) * TBX + (bx - bx0);
       const int vx = s_vx[bl], vy = s_vy[bl];
@@ -348,12 +322,14 @@ __device__ __forceinline__ void sums_phase(const PairBatch& b, const PairJob& jb
       const uint8_t* jrow = J0.p + (size_t)yj * J0.pitch;
       const int xj = x + vx;
       uint32_t iv, jv;
-      if (x + 3 <= W - 1) {
+      if (x + 3 <= x1 - 1) {
         iv = __ldg(reinterpret_cast<const uint32_t*>(irow + x));
         jv = (xj >= 0 && xj + 7 <= lim_w - 1) ? load4_unaligned(jrow, xj) : load4_clamped(jrow, xj, J0.w);
       } else {
-        iv = 0; jv = 0;
-        for (int k = 0; x + k < W; k++) {
+        // ragged end of the row: bytes beyond x1 contribute zero to every sum
+        iv = 0;
+        jv = 0;
+        for (int k = 0; x + k < x1; k++) {
           iv |= (uint32_t)irow[x + k] << (8 * k);
           jv |= (uint32_t)jrow[clampi(xj + k, 0, W - 1)] << (8 * k);
         }
@@ -365,6 +341,13 @@ __device__ __forceinline__ void sums_phase(const PairBatch& b, const PairJob& jb
       sij = __dp4a(iv, jv, sij);
       sab = sad4(iv, jv, sab);
     }
+  };
+  if (fast) {
+    const int xf = nbx * B0, yf = nby * B0;   // end of the full blocks
+    if (xe > xf) region(max(xs, xf), xe, ys, ye);
+    if (ye > yf) region(xs, min(xe, xf), max(ys, yf), ye);
+  } else {
+    region(xs, xe, ys, ye);
   }
   // AMM: one term per block of the tile, from the exact table
   uint32_t samm = 0;

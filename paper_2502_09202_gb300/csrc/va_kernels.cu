@@ -92,7 +92,7 @@ pair_kernel(const PairBatch b) {
   __shared__ unsigned long long s_red[S::NW][kRecWords];
   __shared__ PairJob s_job[2];
   // refinement windows: level side 16 with radius 2 is the largest fast case
-  __shared__ uint32_t s_win[NB * 20 * 6];
+  __shared__ uint32_t s_win[NB * kRefineWinWords];
   // I tiles of levels 0 and 1 (fast path: 3 levels, radius 2), staged asynchronously
   __shared__ __align__(16) uint32_t s_i0[2][TBY * 16 * TBX * 4];
   __shared__ __align__(16) uint32_t s_i1[2][TBY * 8 * TBX * 2];
@@ -202,9 +202,10 @@ pair_kernel(const PairBatch b) {
     }
 
     // ---- phase B: refinement at levels L-2 .. 0 -------------------------------
+    uint32_t part[6] = {0, 0, 0, 0, 0, 0};
     if (fast) {
-      refine_level<8, 2, NT, NB, TBX>(jb.J[1], ti1, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_best32, s_win, tid);
-      refine_level<16, 2, NT, NB, TBX>(jb.J[0], ti0, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_best32, s_win, tid);
+      refine_level<8, 2, NT, NB, TBX, false>(jb.J[1], ti1, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part, tid);
+      refine_level<16, 2, NT, NB, TBX, true>(jb.J[0], ti0, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part, tid);
     } else {
       for (int l = L - 2; l >= 0; l--) {
         const Plane Il = jb.I[l], Jl = jb.J[l];
@@ -251,7 +252,8 @@ pair_kernel(const PairBatch b) {
       }
     }
 
-    sums_phase<TBX, TBY, NT>(b, jb, bx0, by0, B0, fast, ti0, s_vx, s_vy, s_red, tid);
+    __syncthreads();   // every block's vector is read below
+    sums_phase<TBX, TBY, NT>(b, jb, bx0, by0, B0, fast, part, s_vx, s_vy, s_red, tid);
   }
 }
 

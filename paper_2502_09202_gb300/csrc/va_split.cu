@@ -9,6 +9,10 @@
 // Arithmetic and candidate order are those of the fused pair kernel.
 #include "va_device.cuh"
 
+#ifndef VA_REFINE_MINB
+#define VA_REFINE_MINB 8
+#endif
+
 namespace va {
 namespace {
 
@@ -25,15 +29,18 @@ template <int TBX, int TBY>
 struct RefineShape {
   static constexpr int NB = TBX * TBY;
   static constexpr int NT = NB * 4 < 64 ? 64 : NB * 4;   // one level-0 task (block, column) per thread
+  static constexpr int MINB = VA_REFINE_MINB * 128 / NT;  // resident CTAs per SM the register budget allows
 };
 
+// The job holding `item` (the last job whose first item is <= item): each
+// warp compares 32 jobs per step with one ballot.  Called by whole warps.
 __device__ __forceinline__ int find_job(const PairBatch& b, int item) {
-  int lo = 0, hi = b.njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (b.jobs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+  const int lane = threadIdx.x & 31;
+  for (int base = 0;; base += 32) {
+    const int j = base + lane;
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, j < b.njobs && b.jobs[j].item_begin <= item);
+    if (m != 0xFFFFFFFFu || base + 32 >= b.njobs) return base + __popc(m) - 1;
   }
-  return lo;
 }
 
 template <int NT>
@@ -84,13 +91,12 @@ __global__ void __launch_bounds__(CoarseShape<R, TBX, TBY>::NT) coarse_kernel(co
 }
 
 template <int TBX, int TBY>
-__global__ void __launch_bounds__(RefineShape<TBX, TBY>::NT) refine_kernel(const PairBatch b) {
+__global__ void __launch_bounds__(RefineShape<TBX, TBY>::NT, RefineShape<TBX, TBY>::MINB) refine_kernel(const PairBatch b) {
   using S = RefineShape<TBX, TBY>;
   constexpr int NB = S::NB, NT = S::NT;
   __shared__ __align__(16) uint32_t s_i0[TBY * 16 * TBX * 4];
   __shared__ __align__(16) uint32_t s_i1[TBY * 8 * TBX * 2];
-  __shared__ uint32_t s_win[NB * 20 * 6];
-  __shared__ uint32_t s_best32[NB];
+  __shared__ uint32_t s_win[NB * kRefineWinWords];
   __shared__ int s_vx[NB], s_vy[NB];
   __shared__ unsigned long long s_red[NT / 32][kRecWords];
   __shared__ PairJob s_job;
@@ -122,9 +128,11 @@ __global__ void __launch_bounds__(RefineShape<TBX, TBY>::NT) refine_kernel(const
   cp_async_wait_all();
   __syncthreads();
   const int lam = b.cfg.lambda;
-  refine_level<8, 2, NT, NB, TBX>(jb.J[1], s_i1, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_best32, s_win, tid);
-  refine_level<16, 2, NT, NB, TBX>(jb.J[0], s_i0, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_best32, s_win, tid);
-  sums_phase<TBX, TBY, NT>(b, jb, bx0, by0, 16, true, s_i0, s_vx, s_vy, s_red, tid);
+  uint32_t part[6] = {0, 0, 0, 0, 0, 0};
+  refine_level<8, 2, NT, NB, TBX, false>(jb.J[1], s_i1, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part, tid);
+  refine_level<16, 2, NT, NB, TBX, true>(jb.J[0], s_i0, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part, tid);
+  __syncthreads();   // every block's vector is read below
+  sums_phase<TBX, TBY, NT>(b, jb, bx0, by0, 16, true, part, s_vx, s_vy, s_red, tid);
 }
 
 }  // namespace
