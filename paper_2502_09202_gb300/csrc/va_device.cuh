@@ -215,23 +215,33 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
   __syncwarp();   // the next level's lanes read s_vx/s_vy and rewrite the window
 }
 
+// Multiplier of the coarse candidate keys: key = cost * kCoarseKeyM + tb with
+// tb = (|v|_1 << 12) | (vy + R) << 6 | (vx + R) < 2^18 < kCoarseKeyM, so keys
+// order exactly as (cost, |v|_1, vy, vx), and tb = key mod kCoarseKeyM.  A
+// multiplier that is not a power of two makes the key one integer multiply-add,
+// which runs beside the SAD instructions instead of on their pipe.  Keys stay
+// below 2^32 for cost <= 16*255 + 64*2*24.
+constexpr uint32_t kCoarseKeyM = (1u << 18) + 1u;
+
 // Exhaustive search of every block of a tile on the coarsest level (block
 // side 4, radius R): a thread owns one block and 4 consecutive vx candidates
-// and slides down the staged window rows; candidate keys are
-// (cost << 18) | (|v|_1 << 12) | (vy + R) << 6 | (vx + R), i.e. the order
-// (cost, |v|_1, vy, vx).  Expects s_best32 set to all ones and a barrier before
-// the call; leaves the coarse vectors in s_vx/s_vy (after a barrier).
-template <int R, int TBX, int TBY, int NT>
+// and slides down the staged window rows.  With SHIFTED the window is staged
+// as four copies, copy j (at jwin + j * WROWS * WWORDS) holding the rows
+// shifted by j bytes; otherwise the shifts are taken here.  Expects s_best32
+// set to all ones and a barrier before the call; leaves the coarse vectors in
+// s_vx/s_vy (after a barrier).
+template <int R, int TBX, int TBY, int NT, bool SHIFTED>
 __device__ __forceinline__ void coarse_phase(const uint32_t* jwin, const uint32_t* iwin, int bx0, int by0, int nbx,
-                                         int nby, int lam, uint32_t* s_best32, int* s_vx, int* s_vy, int tid) {
+                                             int nby, int lam, uint32_t* s_best32, int* s_vx, int* s_vy, int tid) {
   constexpr int G = (2 * R + 4) / 4, NB = TBX * TBY, NA = NB * G, WWORDS = TBX + G;
+  constexpr int WROWS = TBY * 4 + 2 * R;
   const bool in_a = tid < NA;
   const int g = tid % G, bl = in_a ? tid / G : 0;
   const int bxl = bl % TBX, byl = bl / TBX;
   const bool active = in_a && (bx0 + bxl < nbx) && (by0 + byl < nby);
   const uint32_t i0 = iwin[(byl * 4 + 0) * TBX + bxl], i1 = iwin[(byl * 4 + 1) * TBX + bxl];
   const uint32_t i2 = iwin[(byl * 4 + 2) * TBX + bxl], i3 = iwin[(byl * 4 + 3) * TBX + bxl];
-  const uint32_t lam18 = (uint32_t)lam << 18;
+  const uint32_t lamM = (uint32_t)lam * kCoarseKeyM;
   // acc[j][c & 3] holds candidate c = dy - k (vy = c - R): it receives row k
   // of the block at window row dy, starts at k = 0 and completes at k = 3.
   uint32_t acc[4][4];
@@ -245,12 +255,17 @@ __device__ __forceinline__ void coarse_phase(const uint32_t* jwin, const uint32_
   const uint32_t* wrow = jwin + (byl * 4) * WWORDS + bxl + g;
 #pragma unroll
   for (int dy = 0; dy < 2 * R + 4; dy++) {
-    const uint32_t wlo = wrow[dy * WWORDS], whi = wrow[dy * WWORDS + 1];
     uint32_t w[4];
-    w[0] = wlo;
-    w[1] = __funnelshift_r(wlo, whi, 8);
-    w[2] = __funnelshift_r(wlo, whi, 16);
-    w[3] = __funnelshift_r(wlo, whi, 24);
+    if constexpr (SHIFTED) {
+#pragma unroll
+      for (int j = 0; j < 4; j++) w[j] = wrow[j * (WROWS * WWORDS) + dy * WWORDS];
+    } else {
+      const uint32_t wlo = wrow[dy * WWORDS], whi = wrow[dy * WWORDS + 1];
+      w[0] = wlo;
+      w[1] = __funnelshift_r(wlo, whi, 8);
+      w[2] = __funnelshift_r(wlo, whi, 16);
+      w[3] = __funnelshift_r(wlo, whi, 24);
+    }
 #pragma unroll
     for (int j = 0; j < 4; j++) {
       if (dy <= 2 * R) acc[j][dy & 3] = sad4(i0, w[j], 0u);
@@ -261,9 +276,9 @@ __device__ __forceinline__ void coarse_phase(const uint32_t* jwin, const uint32_
     if (dy >= 3) {
       const int vy = dy - R - 3;
       const int avy = vy < 0 ? -vy : vy;
-      const uint32_t bv = lam18 * (uint32_t)avy + (((uint32_t)avy << 12) | ((uint32_t)(vy + R) << 6));
+      const uint32_t bv = lamM * (uint32_t)avy + (((uint32_t)avy << 12) | ((uint32_t)(vy + R) << 6));
 #pragma unroll
-      for (int j = 0; j < 4; j++) best[j] = min(best[j], (acc[j][(dy - 3) & 3] << 18) + bv);
+      for (int j = 0; j < 4; j++) best[j] = min(best[j], acc[j][(dy - 3) & 3] * kCoarseKeyM + bv);
     }
   }
   uint32_t tbest = 0xFFFFFFFFu;
@@ -272,16 +287,16 @@ __device__ __forceinline__ void coarse_phase(const uint32_t* jwin, const uint32_
     const int vx = -R + 4 * g + j;
     if (vx <= R) {
       const int avx = vx < 0 ? -vx : vx;
-      const uint32_t a = (((uint32_t)(lam * avx)) << 18) + ((uint32_t)avx << 12) + (uint32_t)(vx + R);
+      const uint32_t a = lamM * (uint32_t)avx + ((uint32_t)avx << 12) + (uint32_t)(vx + R);
       tbest = min(tbest, best[j] + a);
     }
   }
   if (active) atomicMin(&s_best32[bl], tbest);
   __syncthreads();
   for (int i = tid; i < NB; i += NT) {
-    const uint32_t k = s_best32[i];
-    s_vx[i] = (int)(k & 63u) - R;
-    s_vy[i] = (int)((k >> 6) & 63u) - R;
+    const uint32_t tb = s_best32[i] % kCoarseKeyM;
+    s_vx[i] = (int)(tb & 63u) - R;
+    s_vy[i] = (int)((tb >> 6) & 63u) - R;
   }
   __syncthreads();
 }

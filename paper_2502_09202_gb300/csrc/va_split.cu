@@ -9,6 +9,9 @@
 // Arithmetic and candidate order are those of the fused pair kernel.
 #include "va_device.cuh"
 
+#ifndef VA_COARSE_MINB
+#define VA_COARSE_MINB 7
+#endif
 #ifndef VA_REFINE_MINB
 #define VA_REFINE_MINB 8
 #endif
@@ -23,6 +26,7 @@ struct CoarseShape {
   static constexpr int NT = (NB * G + 31) / 32 * 32;
   static constexpr int WROWS = TBY * kCoarseSide + 2 * R;
   static constexpr int WWORDS = TBX + G;
+  static constexpr int MINB = VA_COARSE_MINB * 288 / NT > 0 ? VA_COARSE_MINB * 288 / NT : 1;  // resident CTAs per SM
 };
 
 template <int TBX, int TBY>
@@ -50,10 +54,10 @@ __device__ __forceinline__ void copy_job(const PairBatch& b, int item, PairJob* 
 }
 
 template <int R, int TBX, int TBY>
-__global__ void __launch_bounds__(CoarseShape<R, TBX, TBY>::NT) coarse_kernel(const PairBatch b) {
+__global__ void __launch_bounds__(CoarseShape<R, TBX, TBY>::NT, CoarseShape<R, TBX, TBY>::MINB) coarse_kernel(const PairBatch b) {
   using S = CoarseShape<R, TBX, TBY>;
   constexpr int NB = S::NB, NT = S::NT, WROWS = S::WROWS, WWORDS = S::WWORDS;
-  __shared__ uint32_t s_jwin[WROWS * WWORDS];
+  __shared__ uint32_t s_jwin[4 * WROWS * WWORDS];   // the window shifted by 0..3 bytes
   __shared__ uint32_t s_iw[TBY * kCoarseSide * TBX];
   __shared__ uint32_t s_best32[NB];
   __shared__ int s_vx[NB], s_vy[NB];
@@ -71,8 +75,18 @@ __global__ void __launch_bounds__(CoarseShape<R, TBX, TBY>::NT) coarse_kernel(co
     const int wy = c / WWORDS, wx = c - wy * WWORDS;
     const int y = clampi(Yw0 + wy, 0, J2.h - 1), x = Xw0 + 4 * wx;
     const uint8_t* row = J2.p + (size_t)y * J2.pitch;
-    s_jwin[c] = (x >= 0 && x + 3 <= J2.w - 1) ? __ldg(reinterpret_cast<const uint32_t*>(row + x))
-                                              : load4_clamped(row, x, J2.w);
+    uint32_t w0, w1;
+    if (x >= 0 && x + 7 <= J2.w - 1) {
+      w0 = __ldg(reinterpret_cast<const uint32_t*>(row + x));
+      w1 = __ldg(reinterpret_cast<const uint32_t*>(row + x + 4));
+    } else {
+      w0 = load4_clamped(row, x, J2.w);
+      w1 = load4_clamped(row, x + 4, J2.w);
+    }
+    s_jwin[c] = w0;
+    s_jwin[WROWS * WWORDS + c] = __funnelshift_r(w0, w1, 8);
+    s_jwin[2 * WROWS * WWORDS + c] = __funnelshift_r(w0, w1, 16);
+    s_jwin[3 * WROWS * WWORDS + c] = __funnelshift_r(w0, w1, 24);
   }
   for (int c = tid; c < TBY * kCoarseSide * TBX; c += NT) {
     const int r = c / TBX, k = c - r * TBX;
@@ -83,7 +97,7 @@ __global__ void __launch_bounds__(CoarseShape<R, TBX, TBY>::NT) coarse_kernel(co
   }
   for (int i = tid; i < NB; i += NT) s_best32[i] = 0xFFFFFFFFu;
   __syncthreads();
-  coarse_phase<R, TBX, TBY, NT>(s_jwin, s_iw, bx0, by0, nbx, nby, b.cfg.lambda, s_best32, s_vx, s_vy, tid);
+  coarse_phase<R, TBX, TBY, NT, true>(s_jwin, s_iw, bx0, by0, nbx, nby, b.cfg.lambda, s_best32, s_vx, s_vy, tid);
   for (int i = tid; i < NB; i += NT) {
     const int bx = bx0 + i % TBX, by = by0 + i / TBX;
     if (bx < nbx && by < nby) jb.cvec[(size_t)by * nbx + bx] = make_short2((short)s_vx[i], (short)s_vy[i]);
