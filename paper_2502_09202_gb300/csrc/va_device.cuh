@@ -245,10 +245,11 @@ __device__ __forceinline__ void coarse_phase(const uint32_t* jwin, const uint32_
   // acc[j][c & 3] holds candidate c = dy - k (vy = c - R): it receives row k
   // of the block at window row dy, starts at k = 0 and completes at k = 3.
   uint32_t acc[4][4];
-  uint32_t best[4];
+  uint32_t best[4], pend[4];   // pend: the previous row's keys, folded in pairs by a 3-input minimum
 #pragma unroll
   for (int j = 0; j < 4; j++) {
     best[j] = 0xFFFFFFFFu;
+    pend[j] = 0xFFFFFFFFu;
 #pragma unroll
     for (int k = 0; k < 4; k++) acc[j][k] = 0;
   }
@@ -278,7 +279,11 @@ __device__ __forceinline__ void coarse_phase(const uint32_t* jwin, const uint32_
       const int avy = vy < 0 ? -vy : vy;
       const uint32_t bv = lamM * (uint32_t)avy + (((uint32_t)avy << 12) | ((uint32_t)(vy + R) << 6));
 #pragma unroll
-      for (int j = 0; j < 4; j++) best[j] = min(best[j], acc[j][(dy - 3) & 3] * kCoarseKeyM + bv);
+      for (int j = 0; j < 4; j++) {
+        const uint32_t key = acc[j][(dy - 3) & 3] * kCoarseKeyM + bv;
+        if (((dy - 3) & 1) == 0 && dy < 2 * R + 3) pend[j] = key;
+        else best[j] = __vimin3_u32(best[j], pend[j], key);
+      }
     }
   }
   uint32_t tbest = 0xFFFFFFFFu;
