@@ -35,6 +35,25 @@ def _env_rank():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def reduce_max_over_ranks(values, world, device=None):
+    """Each value's maximum over all ranks (all_reduce MAX: nccl on GPUs, gloo on CPU);
+    this rank's values when world == 1."""
+    values = [float(v) for v in values]
+    if world <= 1:
+        return values
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu().tolist()]
+
+
+def job_throughput(world, frames_per_rank, ms_per_step):
+    """Whole-job frames/s of the replica layout: every rank analyses its own clip of
+    `frames_per_rank` frames (weak scaling) and a step lasts as long as the slowest rank."""
+    return world * frames_per_rank / (ms_per_step / 1000.0)
+
+
 def _spec():
     from paper_2502_09202_gb300 import synth
     return synth.config_interlaced()
@@ -385,12 +404,6 @@ def run_gpu(args):
         torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * T / (ms / 1000.0)
 
     # --- end to end through host buffers --------------------------------------------------
     for _ in range(max(1, args.warmup // 2)):
@@ -407,7 +420,10 @@ def run_gpu(args):
     torch.cuda.synchronize()
     barrier()
     ms_e2e = e2.elapsed_time(e3) / args.steps
-    e2e_value = world * T / (ms_e2e / 1000.0)
+    # the job's step time is the slowest rank's
+    ms, ms_e2e = reduce_max_over_ranks([ms, ms_e2e], world, device=f"cuda:{local}")
+    value = job_throughput(world, T, ms)
+    e2e_value = job_throughput(world, T, ms_e2e)
 
     # roofline of the dominant kernel (fused pair kernel): algorithmic |a-b| accumulates per launch
     pair_ms = sum(p["pair_kernel_ms"] for p in profs)
