@@ -223,52 +223,38 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
 // below 2^32 for cost <= 16*255 + 64*2*24.
 constexpr uint32_t kCoarseKeyM = (1u << 18) + 1u;
 
-// Exhaustive search of every block of a tile on the coarsest level (block
-// side 4, radius R): a thread owns one block and 4 consecutive vx candidates
-// and slides down the staged window rows.  With SHIFTED the window is staged
-// as four copies, copy j (at jwin + j * WROWS * WWORDS) holding the rows
-// shifted by j bytes; otherwise the shifts are taken here.  Expects s_best32
-// set to all ones and a barrier before the call; leaves the coarse vectors in
-// s_vx/s_vy (after a barrier).
-template <int R, int TBX, int TBY, int NT, bool SHIFTED>
-__device__ __forceinline__ void coarse_phase(const uint32_t* jwin, const uint32_t* iwin, int bx0, int by0, int nbx,
-                                             int nby, int lam, uint32_t* s_best32, int* s_vx, int* s_vy, int tid) {
-  constexpr int G = (2 * R + 4) / 4, NB = TBX * TBY, NA = NB * G, WWORDS = TBX + G;
-  constexpr int WROWS = TBY * 4 + 2 * R;
-  const bool in_a = tid < NA;
-  const int g = tid % G, bl = in_a ? tid / G : 0;
-  const int bxl = bl % TBX, byl = bl / TBX;
-  const bool active = in_a && (bx0 + bxl < nbx) && (by0 + byl < nby);
-  const uint32_t i0 = iwin[(byl * 4 + 0) * TBX + bxl], i1 = iwin[(byl * 4 + 1) * TBX + bxl];
-  const uint32_t i2 = iwin[(byl * 4 + 2) * TBX + bxl], i3 = iwin[(byl * 4 + 3) * TBX + bxl];
-  const uint32_t lamM = (uint32_t)lam * kCoarseKeyM;
+// Rows of the coarse search for one block and NJ consecutive vx candidates
+// starting at vx0: slides down the staged window rows from `wrow` (the block's
+// first row, word of vx0) and returns the smallest key.  With SHIFTED the
+// window is staged as four copies, copy j (at +j * COPY words) holding the
+// rows shifted by j bytes; otherwise the shifts are taken here.
+template <int R, int NJ, int WWORDS, int COPY, bool SHIFTED>
+__device__ __forceinline__ uint32_t coarse_rows(const uint32_t* wrow, uint32_t i0, uint32_t i1, uint32_t i2,
+                                                uint32_t i3, int vx0, uint32_t lamM) {
   // acc[j][c & 3] holds candidate c = dy - k (vy = c - R): it receives row k
   // of the block at window row dy, starts at k = 0 and completes at k = 3.
-  uint32_t acc[4][4];
-  uint32_t best[4], pend[4];   // pend: the previous row's keys, folded in pairs by a 3-input minimum
+  uint32_t acc[NJ][4];
+  uint32_t best[NJ], pend[NJ];   // pend: the previous row's keys, folded in pairs by a 3-input minimum
 #pragma unroll
-  for (int j = 0; j < 4; j++) {
+  for (int j = 0; j < NJ; j++) {
     best[j] = 0xFFFFFFFFu;
     pend[j] = 0xFFFFFFFFu;
 #pragma unroll
     for (int k = 0; k < 4; k++) acc[j][k] = 0;
   }
-  const uint32_t* wrow = jwin + (byl * 4) * WWORDS + bxl + g;
 #pragma unroll
   for (int dy = 0; dy < 2 * R + 4; dy++) {
-    uint32_t w[4];
-    if constexpr (SHIFTED) {
+    uint32_t w[NJ];
+    if constexpr (SHIFTED || NJ == 1) {
 #pragma unroll
-      for (int j = 0; j < 4; j++) w[j] = wrow[j * (WROWS * WWORDS) + dy * WWORDS];
+      for (int j = 0; j < NJ; j++) w[j] = wrow[j * COPY + dy * WWORDS];
     } else {
       const uint32_t wlo = wrow[dy * WWORDS], whi = wrow[dy * WWORDS + 1];
-      w[0] = wlo;
-      w[1] = __funnelshift_r(wlo, whi, 8);
-      w[2] = __funnelshift_r(wlo, whi, 16);
-      w[3] = __funnelshift_r(wlo, whi, 24);
+#pragma unroll
+      for (int j = 0; j < NJ; j++) w[j] = j ? __funnelshift_r(wlo, whi, 8 * j) : wlo;
     }
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
+    for (int j = 0; j < NJ; j++) {
       if (dy <= 2 * R) acc[j][dy & 3] = sad4(i0, w[j], 0u);
       if (dy >= 1 && dy - 1 <= 2 * R) acc[j][(dy - 1) & 3] = sad4(i1, w[j], acc[j][(dy - 1) & 3]);
       if (dy >= 2 && dy - 2 <= 2 * R) acc[j][(dy - 2) & 3] = sad4(i2, w[j], acc[j][(dy - 2) & 3]);
@@ -279,7 +265,7 @@ __device__ __forceinline__ void coarse_phase(const uint32_t* jwin, const uint32_
       const int avy = vy < 0 ? -vy : vy;
       const uint32_t bv = lamM * (uint32_t)avy + (((uint32_t)avy << 12) | ((uint32_t)(vy + R) << 6));
 #pragma unroll
-      for (int j = 0; j < 4; j++) {
+      for (int j = 0; j < NJ; j++) {
         const uint32_t key = acc[j][(dy - 3) & 3] * kCoarseKeyM + bv;
         if (((dy - 3) & 1) == 0 && dy < 2 * R + 3) pend[j] = key;
         else best[j] = __vimin3_u32(best[j], pend[j], key);
@@ -288,14 +274,42 @@ __device__ __forceinline__ void coarse_phase(const uint32_t* jwin, const uint32_
   }
   uint32_t tbest = 0xFFFFFFFFu;
 #pragma unroll
-  for (int j = 0; j < 4; j++) {
-    const int vx = -R + 4 * g + j;
-    if (vx <= R) {
-      const int avx = vx < 0 ? -vx : vx;
-      const uint32_t a = lamM * (uint32_t)avx + ((uint32_t)avx << 12) + (uint32_t)(vx + R);
-      tbest = min(tbest, best[j] + a);
-    }
+  for (int j = 0; j < NJ; j++) {
+    const int vx = vx0 + j;
+    const int avx = vx < 0 ? -vx : vx;
+    const uint32_t a = lamM * (uint32_t)avx + ((uint32_t)avx << 12) + (uint32_t)(vx + R);
+    tbest = min(tbest, best[j] + a);
   }
+  return tbest;
+}
+
+// Exhaustive search of every block of a tile on the coarsest level (block
+// side 4, radius R): threads [0, NB*R/2) own one block and 4 consecutive vx
+// candidates each (vx = -R .. R-1), threads [NB*R/2, NB*R/2 + NB) one block
+// and the last column vx = +R (a whole warp or warps: the split is a multiple
+// of 32 threads).  Window layout as in coarse_rows.  Expects s_best32 set to
+// all ones and a barrier before the call; leaves the coarse vectors in
+// s_vx/s_vy (after a barrier).
+template <int R, int TBX, int TBY, int NT, bool SHIFTED>
+__device__ __forceinline__ void coarse_phase(const uint32_t* jwin, const uint32_t* iwin, int bx0, int by0, int nbx,
+                                             int nby, int lam, uint32_t* s_best32, int* s_vx, int* s_vy, int tid) {
+  constexpr int GQ = R / 2, NB = TBX * TBY, NG = NB * GQ, WWORDS = TBX + GQ + 1;
+  constexpr int COPY = (TBY * 4 + 2 * R) * WWORDS;
+  static_assert(R % 4 == 0 && NG % 32 == 0 && NT >= NG + NB, "coarse thread layout");
+  const bool grouped = tid < NG, last = tid >= NG && tid < NG + NB;
+  const int g = grouped ? tid % GQ : GQ;
+  const int bl = grouped ? tid / GQ : (last ? tid - NG : 0);
+  const int bxl = bl % TBX, byl = bl / TBX;
+  const bool active = (grouped || last) && (bx0 + bxl < nbx) && (by0 + byl < nby);
+  const uint32_t i0 = iwin[(byl * 4 + 0) * TBX + bxl], i1 = iwin[(byl * 4 + 1) * TBX + bxl];
+  const uint32_t i2 = iwin[(byl * 4 + 2) * TBX + bxl], i3 = iwin[(byl * 4 + 3) * TBX + bxl];
+  const uint32_t lamM = (uint32_t)lam * kCoarseKeyM;
+  const uint32_t* wrow = jwin + (byl * 4) * WWORDS + bxl + g;
+  uint32_t tbest = 0xFFFFFFFFu;
+  if (grouped)   // warp-uniform
+    tbest = coarse_rows<R, 4, WWORDS, COPY, SHIFTED>(wrow, i0, i1, i2, i3, -R + 4 * g, lamM);
+  else if (tid < ((NG + NB + 31) & ~31))
+    tbest = coarse_rows<R, 1, WWORDS, COPY, SHIFTED>(wrow, i0, i1, i2, i3, R, lamM);
   if (active) atomicMin(&s_best32[bl], tbest);
   __syncthreads();
   for (int i = tid; i < NB; i += NT) {
