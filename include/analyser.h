@@ -244,6 +244,20 @@ int analyser_detect_offline(const analyser_params* p, int width, int height, int
  */
 int analyser_measure_sad_peak(int device, double* tera_per_s);
 
+/*
+ * Resource cache (the paper has no counterpart: this is library plumbing).
+ * Device buffers, page-locked host buffers, streams and events that an
+ * analyser, server or analyser_measure_pairs call releases go back to a
+ * process-wide cache and are reused by the next one of the same size class,
+ * which avoids cudaMalloc/cudaFree (and the device synchronisation cudaFree
+ * implies) per clip.  analyser_trim_cache() returns the cached device and host
+ * buffers to CUDA (buffers still owned by live analysers or servers are not
+ * touched); analyser_cached_bytes() reports the device bytes held.  Both are
+ * thread-safe and never fail.
+ */
+void analyser_trim_cache(void);
+long long analyser_cached_bytes(void);
+
 /* ---- serving: continuous batching of many clips on one GPU ------------------- */
 
 /* A server admits clips while the device-memory budget allows. */

@@ -6,6 +6,7 @@ results.  PyTorch is used only to hand over device buffers and streams.
 from __future__ import annotations
 
 import ctypes
+from collections.abc import Mapping
 
 import numpy as np
 
@@ -13,7 +14,7 @@ from . import native as N
 from .native import AnalyserError, default_params
 
 __all__ = ["Analyser", "Server", "measure_pairs", "detect_offline", "default_params", "AnalyserError",
-           "results_to_dict", "sad_peak"]
+           "results_to_dict", "sad_peak", "MeasureTable", "trim_cache"]
 
 
 def _check(code: int, where: str, handle=None):
@@ -27,19 +28,53 @@ def _check(code: int, where: str, handle=None):
     return code
 
 
+class MeasureTable(Mapping):
+    """The measures of a clip keyed by (kind, a, b): a read-only mapping over one
+    structured numpy array (``.array``, fields as in the C struct), copied from
+    the library in one piece; a value is built as a dict when it is read."""
+
+    FIELDS = ("si", "sj", "sii", "sjj", "sij", "sabs", "samm", "n", "nb", "ncc", "swr", "amm", "act")
+
+    def __init__(self, array: np.ndarray):
+        self.array = array
+        self._index = None
+
+    def _keys(self) -> dict:
+        if self._index is None:
+            a = self.array
+            self._index = {k: i for i, k in enumerate(zip(a["kind"].tolist(), a["a"].tolist(), a["b"].tolist()))}
+        return self._index
+
+    def __getitem__(self, key):
+        row = self.array[self._keys()[tuple(key)]]
+        return {f: row[f].item() for f in self.FIELDS}
+
+    def __iter__(self):
+        return iter(self._keys())
+
+    def __len__(self):
+        return len(self.array)
+
+    def __contains__(self, key):
+        return tuple(key) in self._keys()
+
+
+def _ints(ptr, n: int) -> list:
+    return np.ctypeslib.as_array(ptr, shape=(n,)).tolist() if n > 0 else []
+
+
 def results_to_dict(r: N.Results) -> dict:
     """Results in the layout the oracle returns (measures keyed by (kind, a, b))."""
-    cuts = [r.cuts[i] for i in range(r.ncuts)]
-    dis = [(r.dissolves[2 * i], r.dissolves[2 * i + 1]) for i in range(r.ndissolves)]
+    cuts = _ints(r.cuts, r.ncuts)
+    d = _ints(r.dissolves, 2 * r.ndissolves)
+    dis = [(d[2 * i], d[2 * i + 1]) for i in range(r.ndissolves)]
     shots = [{"first": s.first, "last": s.last, "label": s.label, "field_order": s.field_order,
               "phase": s.pulldown_phase, "analysed": s.analysed} for s in (r.shots[i] for i in range(r.nshots))]
-    kf = [r.keyframes[i] for i in range(r.nkeyframes)]
-    meas = {}
-    for i in range(r.nmeasures):
-        m = r.measures[i]
-        meas[(m.kind, m.a, m.b)] = {"si": m.si, "sj": m.sj, "sii": m.sii, "sjj": m.sjj, "sij": m.sij,
-                                    "sabs": m.sabs, "samm": m.samm, "n": m.n, "nb": m.nb,
-                                    "ncc": m.ncc, "swr": m.swr, "amm": m.amm, "act": m.act}
+    kf = _ints(r.keyframes, r.nkeyframes)
+    if r.nmeasures > 0:
+        meas = MeasureTable(np.ctypeslib.as_array(r.measures, shape=(r.nmeasures,)).copy())
+    else:
+        meas = MeasureTable(np.zeros(0, dtype=np.dtype(N.Measure)))
     out = {"cuts": cuts, "dissolves": dis, "keyframes": kf, "shots": shots, "label": r.label,
            "field_order": r.field_order, "pulldown_phase": r.pulldown_phase, "measures": meas,
            "nframes": r.nframes}
@@ -166,6 +201,14 @@ def measure_pairs(frames, kinds, ia, ib, params: N.Params | None = None, want_mo
             off += m
         return rec, out
     return rec, None
+
+
+def trim_cache() -> int:
+    """Return the library's cached device and page-locked buffers to CUDA; the
+    device bytes that were cached."""
+    n = int(N.lib.analyser_cached_bytes())
+    N.lib.analyser_trim_cache()
+    return n
 
 
 def sad_peak(device: int = 0) -> float:

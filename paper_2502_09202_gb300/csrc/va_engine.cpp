@@ -1,5 +1,6 @@
 // Runtime of the analyser (see va_engine.h).
 #include "va_engine.h"
+#include "va_pool.h"
 
 #include <algorithm>
 #include <chrono>
@@ -39,6 +40,11 @@ static uint64_t isqrt_digits(uint64_t n) {
     bit >>= 2;
   }
   return res;
+}
+
+// Q(k) = floor(sqrt(k) * 2^16) = isqrt(k * 2^32), k = 0..qmax
+static void build_qtab(uint32_t* q, int qmax) {
+  for (int k = 0; k <= qmax; k++) q[k] = (uint32_t)isqrt_digits((uint64_t)k << 32);
 }
 
 int validate_params(const analyser_params& p, std::string& why) {
@@ -114,26 +120,28 @@ void Geometry::init(int width, int height, int levels, bool own_l0) {
 Engine::Engine(const analyser_params& params) : p(params) {}
 
 Engine::~Engine() {
-  for (Clip* c : clips) if (c->d_ring) cudaFree(c->d_ring);
-  if (d_qtab) cudaFree(d_qtab);
-  if (d_status) cudaFree(d_status);
-  if (h_status) cudaFreeHost(h_status);
-  if (d_pjobs) cudaFree(d_pjobs);
-  if (h_pjobs) cudaFreeHost(h_pjobs);
-  if (d_djobs) cudaFree(d_djobs);
-  if (h_djobs) cudaFreeHost(h_djobs);
-  if (d_rec) cudaFree(d_rec);
-  if (h_rec) cudaFreeHost(h_rec);
-  if (d_vec) cudaFree(d_vec);
-  for (cudaEvent_t& e : ev_)
-    if (e) cudaEventDestroy(e);
-  if (ev_up_) cudaEventDestroy(ev_up_);
-  if (ev_chunk_) cudaEventDestroy(ev_chunk_);
-  if (ev_join_) cudaEventDestroy(ev_join_);
-  if (rstream) cudaStreamDestroy(rstream);
-  if (d_cvec) cudaFree(d_cvec);
-  if (cstream) cudaStreamDestroy(cstream);
-  if (stream) cudaStreamDestroy(stream);
+  // nothing may still run on the engine's streams when their buffers return to the cache
+  if (stream) cudaStreamSynchronize(stream);
+  if (cstream) cudaStreamSynchronize(cstream);
+  if (rstream) cudaStreamSynchronize(rstream);
+  for (Clip* c : clips) pool_free(c->d_ring);
+  pool_free(d_status);
+  pool_free_host(h_status);
+  pool_free(d_pjobs);
+  pool_free_host(h_pjobs);
+  pool_free(d_djobs);
+  pool_free_host(h_djobs);
+  pool_free(d_rec);
+  pool_free_host(h_rec);
+  pool_free(d_vec);
+  pool_free(d_cvec);
+  for (cudaEvent_t& e : ev_) pool_release_event(e);
+  pool_release_event(ev_up_);
+  pool_release_event(ev_chunk_);
+  pool_release_event(ev_join_);
+  pool_release_stream(rstream);
+  pool_release_stream(cstream);
+  pool_release_stream(stream);
 }
 
 void Engine::profile(analyser_profile_t* out) const {
@@ -158,25 +166,22 @@ int Engine::init(std::string& why) {
   int rc = validate_params(p, why);
   if (rc) return rc;
   VA_CUDA_TRY(cudaSetDevice(p.device), why);
-  VA_CUDA_TRY(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking), why);
-  VA_CUDA_TRY(cudaStreamCreateWithFlags(&cstream, cudaStreamNonBlocking), why);
-  VA_CUDA_TRY(cudaStreamCreateWithFlags(&rstream, cudaStreamNonBlocking), why);
-  VA_CUDA_TRY(cudaEventCreateWithFlags(&ev_chunk_, cudaEventDisableTiming), why);
-  VA_CUDA_TRY(cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming), why);
-  VA_CUDA_TRY(cudaEventCreateWithFlags(&ev_up_, cudaEventDisableTiming), why);
+  VA_CUDA_TRY(pool_stream(&stream), why);
+  VA_CUDA_TRY(pool_stream(&cstream), why);
+  VA_CUDA_TRY(pool_stream(&rstream), why);
+  VA_CUDA_TRY(pool_event(&ev_chunk_, false), why);
+  VA_CUDA_TRY(pool_event(&ev_join_, false), why);
+  VA_CUDA_TRY(pool_event(&ev_up_, false), why);
   VA_CUDA_TRY(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, p.device), why);
   // Q(k) = floor(sqrt(k) * 2^16) for every k = vx^2 + vy^2 the search can produce
   int vmax = p.radius_coarse;
   for (int l = p.levels - 2; l >= 0; l--) vmax = 2 * vmax + p.radius_refine;
   qmax = 2 * vmax * vmax;
-  std::vector<uint32_t> q(qmax + 1);
-  for (int k = 0; k <= qmax; k++) q[k] = (uint32_t)isqrt_digits((uint64_t)k << 32);
-  VA_CUDA_TRY(cudaMalloc(&d_qtab, sizeof(uint32_t) * (qmax + 1)), why);
-  VA_CUDA_TRY(cudaMemcpy(d_qtab, q.data(), sizeof(uint32_t) * (qmax + 1), cudaMemcpyHostToDevice), why);
-  VA_CUDA_TRY(cudaMalloc(&d_status, sizeof(int)), why);
-  VA_CUDA_TRY(cudaMemset(d_status, 0, sizeof(int)), why);
-  VA_CUDA_TRY(cudaMallocHost(&h_status, sizeof(int)), why);
-  for (cudaEvent_t& ev : ev_) VA_CUDA_TRY(cudaEventCreate(&ev), why);
+  VA_CUDA_TRY(pool_qtab(qmax, build_qtab, &d_qtab), why);
+  VA_CUDA_TRY(pool_malloc(reinterpret_cast<void**>(&d_status), sizeof(int)), why);
+  VA_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), stream), why);
+  VA_CUDA_TRY(pool_malloc_host(reinterpret_cast<void**>(&h_status), sizeof(int)), why);
+  for (cudaEvent_t& ev : ev_) VA_CUDA_TRY(pool_event(&ev, true), why);
   return ANALYSER_OK;
 }
 
@@ -194,9 +199,8 @@ int Engine::add_clip(Clip* c, std::string& why, bool enlist) {
     why = "rolling window exceeds mem_budget_bytes";
     return ANALYSER_ERR_OOM;
   }
-  cudaError_t e = cudaMalloc(&c->d_ring, bytes);
+  cudaError_t e = pool_malloc(reinterpret_cast<void**>(&c->d_ring), bytes);
   if (e != cudaSuccess) {
-    cudaGetLastError();
     why = std::string("cudaMalloc(window): ") + cudaGetErrorString(e);
     return ANALYSER_ERR_OOM;
   }
@@ -219,7 +223,11 @@ int Engine::add_clip(Clip* c, std::string& why, bool enlist) {
 void Engine::remove_clip(Clip* c) {
   clips.erase(std::remove(clips.begin(), clips.end(), c), clips.end());
   if (c->d_ring) {
-    cudaFree(c->d_ring);
+    // the window returns to the cache: nothing queued may still read or write it
+    cudaStreamSynchronize(stream);
+    cudaStreamSynchronize(cstream);
+    cudaStreamSynchronize(rstream);
+    pool_free(c->d_ring);
     c->d_ring = nullptr;
   }
 }
@@ -340,7 +348,8 @@ void Engine::choose_tile(int width, int height, int* tbx, int* tby) {
           }
           if (ok && tsum < best_s) { best_s = tsum; bx = cd[0]; by = cd[1]; }
         }
-        cudaFree(c.d_ring);
+        cudaStreamSynchronize(stream);
+        pool_free(c.d_ring);
         c.d_ring = nullptr;
       }
       cudaFree(d);
@@ -371,25 +380,27 @@ int Engine::run_alone(Clip* c) {
 int Engine::ensure_capacity(int npairs, int ndown) {
   std::string why;
   if (npairs > cap_pairs) {
+    // no wave is in flight here: the previous buffers are idle
     int nc = std::max(npairs, std::max(256, cap_pairs * 2));
-    if (d_pjobs) cudaFree(d_pjobs);
-    if (h_pjobs) cudaFreeHost(h_pjobs);
-    if (d_rec) cudaFree(d_rec);
-    if (h_rec) cudaFreeHost(h_rec);
+    pool_free(d_pjobs);
+    pool_free_host(h_pjobs);
+    pool_free(d_rec);
+    pool_free_host(h_rec);
     d_pjobs = nullptr; h_pjobs = nullptr; d_rec = nullptr; h_rec = nullptr;
-    VA_CUDA_TRY(cudaMalloc(&d_pjobs, sizeof(PairJob) * nc), message);
-    VA_CUDA_TRY(cudaMallocHost(&h_pjobs, sizeof(PairJob) * nc), message);
-    VA_CUDA_TRY(cudaMalloc(&d_rec, sizeof(unsigned long long) * kRecWords * nc), message);
-    VA_CUDA_TRY(cudaMallocHost(&h_rec, sizeof(unsigned long long) * kRecWords * nc), message);
+    VA_CUDA_TRY(pool_malloc(reinterpret_cast<void**>(&d_pjobs), sizeof(PairJob) * nc), message);
+    VA_CUDA_TRY(pool_malloc_host(reinterpret_cast<void**>(&h_pjobs), sizeof(PairJob) * nc), message);
+    VA_CUDA_TRY(pool_malloc(reinterpret_cast<void**>(&d_rec), sizeof(unsigned long long) * kRecWords * nc), message);
+    VA_CUDA_TRY(pool_malloc_host(reinterpret_cast<void**>(&h_rec), sizeof(unsigned long long) * kRecWords * nc),
+                message);
     cap_pairs = nc;
   }
   if (ndown > cap_down) {
     int nc = std::max(ndown, std::max(256, cap_down * 2));
-    if (d_djobs) cudaFree(d_djobs);
-    if (h_djobs) cudaFreeHost(h_djobs);
+    pool_free(d_djobs);
+    pool_free_host(h_djobs);
     d_djobs = nullptr; h_djobs = nullptr;
-    VA_CUDA_TRY(cudaMalloc(&d_djobs, sizeof(DownJob) * nc), message);
-    VA_CUDA_TRY(cudaMallocHost(&h_djobs, sizeof(DownJob) * nc), message);
+    VA_CUDA_TRY(pool_malloc(reinterpret_cast<void**>(&d_djobs), sizeof(DownJob) * nc), message);
+    VA_CUDA_TRY(pool_malloc_host(reinterpret_cast<void**>(&h_djobs), sizeof(DownJob) * nc), message);
     cap_down = nc;
   }
   return ANALYSER_OK;
@@ -517,9 +528,9 @@ int Engine::wave_launch() {
     }
   }
   if (vec_total > cap_vec) {
-    if (d_vec) cudaFree(d_vec);
+    pool_free(d_vec);
     d_vec = nullptr;
-    if (cudaMalloc(&d_vec, sizeof(short2) * vec_total) != cudaSuccess) {
+    if (pool_malloc(reinterpret_cast<void**>(&d_vec), sizeof(short2) * vec_total) != cudaSuccess) {
       status = ANALYSER_ERR_OOM; message = "cudaMalloc(motion dump)"; return status;
     }
     cap_vec = vec_total;
@@ -536,9 +547,9 @@ int Engine::wave_launch() {
     cvec_total += (size_t)(g.W / g.B0) * (h0 / g.B0);
   }
   if (split && cvec_total > cap_cvec) {
-    if (d_cvec) cudaFree(d_cvec);
+    pool_free(d_cvec);
     d_cvec = nullptr;
-    if (cudaMalloc(&d_cvec, sizeof(short2) * cvec_total) != cudaSuccess) {
+    if (pool_malloc(reinterpret_cast<void**>(&d_cvec), sizeof(short2) * cvec_total) != cudaSuccess) {
       status = ANALYSER_ERR_OOM; message = "cudaMalloc(coarse vectors)"; return status;
     }
     cap_cvec = cvec_total;
@@ -786,7 +797,11 @@ int Engine::measure_pairs(int width, int height, const uint8_t* frames, long lon
   attach_device(&c, frames, pitch, stride, nframes);
   for (int i = 0; i < npairs; i++) c.pending.push_back(pair_key(kinds[i], ia[i], ib[i]));
   rc = run_alone(&c);
-  if (c.d_ring) { cudaFree(c.d_ring); c.d_ring = nullptr; }
+  if (c.d_ring) {
+    cudaStreamSynchronize(stream);
+    pool_free(c.d_ring);
+    c.d_ring = nullptr;
+  }
   stream = saved;
   if (rc < 0 || status) {
     why = message;

@@ -138,7 +138,7 @@ class Engine {
                      short2* vec);
 
   // device tables
-  uint32_t* d_qtab = nullptr;
+  const uint32_t* d_qtab = nullptr;   // shared, owned by the resource cache
   int qmax = 0;
   int* d_status = nullptr;
   int* h_status = nullptr;

@@ -237,3 +237,28 @@ def test_split_and_fused_kernels_match_the_oracle(mode):
         a.push(frames)
         a.finish()
         _compare_results(a.results(), OA.analyse_frames(frames))
+
+
+def test_cached_buffers_reused_across_clips_and_trimmed():
+    """Analysers and stateless calls created one after another run on buffers the
+    previous ones returned to the resource cache (not cleared): results stay
+    exact, and trimming returns the cached device memory."""
+    api = _api()
+    spec = synth.config_small()
+    frames = synth.Clip(spec).frames()
+    ref = OA.analyse_frames(frames)
+    other = synth.Clip(synth.ClipSpec(333, 190, 5, 25.0, synth.TFF, 3, 3.0,
+                                      synth.SceneStyle(n_objects=(4, 6), obj_speed=10, cell=8, bg_kind="textured")))
+    of = other.frames()
+    for rep in range(3):
+        with api.Analyser(spec.width, spec.height, spec.fps) as a:
+            a.push_device(_dev(frames))
+            a.finish()
+            _compare_results(a.results(), ref)
+        rec, _ = api.measure_pairs(_dev(of), [0, 1], [0, 2], [1, 3])
+        for k, (kind, i, j) in enumerate([(0, 0, 1), (1, 2, 3)]):
+            r, _ = _oracle_pair(kind, of[i], of[j])
+            assert list(rec[k]) == [r[f] for f in REC7], rep
+    assert api.N.lib.analyser_cached_bytes() > 0
+    assert api.trim_cache() > 0
+    assert api.N.lib.analyser_cached_bytes() == 0

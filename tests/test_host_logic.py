@@ -26,7 +26,7 @@ def native():
 def _declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:int|void)\s+\(?\*?\s*([a-z_]+)\s*\(", text, flags=re.M)
+    names = re.findall(r"^\s*(?:int|void|long long)\s+\(?\*?\s*([a-z_]+)\s*\(", text, flags=re.M)
     return sorted(set(n for n in names if not n.endswith("_fn")))
 
 
