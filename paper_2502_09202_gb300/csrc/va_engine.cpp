@@ -131,6 +131,8 @@ Engine::~Engine() {
   pool_free_host(h_pjobs);
   pool_free(d_djobs);
   pool_free_host(h_djobs);
+  pool_free(d_pyjobs);
+  pool_free_host(h_pyjobs);
   pool_free(d_rec);
   pool_free_host(h_rec);
   pool_free(d_vec);
@@ -377,7 +379,7 @@ int Engine::run_alone(Clip* c) {
   return status ? status : rc;
 }
 
-int Engine::ensure_capacity(int npairs, int ndown) {
+int Engine::ensure_capacity(int npairs, int ndown, int npyr) {
   std::string why;
   if (npairs > cap_pairs) {
     // no wave is in flight here: the previous buffers are idle
@@ -402,6 +404,15 @@ int Engine::ensure_capacity(int npairs, int ndown) {
     VA_CUDA_TRY(pool_malloc(reinterpret_cast<void**>(&d_djobs), sizeof(DownJob) * nc), message);
     VA_CUDA_TRY(pool_malloc_host(reinterpret_cast<void**>(&h_djobs), sizeof(DownJob) * nc), message);
     cap_down = nc;
+  }
+  if (npyr > cap_pyr) {
+    int nc = std::max(npyr, std::max(256, cap_pyr * 2));
+    pool_free(d_pyjobs);
+    pool_free_host(h_pyjobs);
+    d_pyjobs = nullptr; h_pyjobs = nullptr;
+    VA_CUDA_TRY(pool_malloc(reinterpret_cast<void**>(&d_pyjobs), sizeof(PyrJob) * nc), message);
+    VA_CUDA_TRY(pool_malloc_host(reinterpret_cast<void**>(&h_pyjobs), sizeof(PyrJob) * nc), message);
+    cap_pyr = nc;
   }
   return ANALYSER_OK;
 }
@@ -468,6 +479,7 @@ int Engine::wave_launch() {
   }
   // ---- gather ---------------------------------------------------------------
   std::vector<DownJob> down[kMaxLevels];
+  pyr_.clear();
   for (Clip* c : clips) {
     if (c->status || c->done()) continue;
     const Geometry& g = c->geo;
@@ -476,11 +488,22 @@ int Engine::wave_launch() {
       uint8_t* base = c->d_ring + (size_t)s * g.slot_bytes;
       const uint8_t* l0 = c->l0[s];
       const int p0 = c->l0_pitch[s];
-      // level 1 from level 0: frame, upper field, lower field
-      down[1].push_back({{l0, p0, g.W, g.H}, base + g.off_f[1], g.fp[1]});
-      down[1].push_back({{l0, 2 * p0, g.W, g.H / 2}, base + g.off_u[1], g.gp[1]});
-      down[1].push_back({{l0 + p0, 2 * p0, g.W, g.H / 2}, base + g.off_l[1], g.gp[1]});
-      for (int l = 2; l < g.L; l++) {
+      if (g.L < 2) continue;
+      // levels 1 and 2 of the frame and both fields from one read of level 0
+      PyrJob pj;
+      pj.l0 = l0;
+      pj.l0_pitch = p0;
+      pj.w = g.W;
+      pj.h = g.H;
+      const bool two = g.L >= 3;
+      pj.out[0] = base + g.off_f[1]; pj.pitch[0] = g.fp[1];
+      pj.out[2] = base + g.off_u[1]; pj.pitch[2] = g.gp[1];
+      pj.out[4] = base + g.off_l[1]; pj.pitch[4] = g.gp[1];
+      pj.out[1] = two ? base + g.off_f[2] : nullptr; pj.pitch[1] = two ? g.fp[2] : 0;
+      pj.out[3] = two ? base + g.off_u[2] : nullptr; pj.pitch[3] = two ? g.gp[2] : 0;
+      pj.out[5] = two ? base + g.off_l[2] : nullptr; pj.pitch[5] = two ? g.gp[2] : 0;
+      pyr_.push_back(pj);
+      for (int l = 3; l < g.L; l++) {
         down[l].push_back({{base + g.off_f[l - 1], g.fp[l - 1], g.fw[l - 1], g.fh[l - 1]}, base + g.off_f[l], g.fp[l]});
         down[l].push_back({{base + g.off_u[l - 1], g.gp[l - 1], g.gw[l - 1], g.gh[l - 1]}, base + g.off_u[l], g.gp[l]});
         down[l].push_back({{base + g.off_l[l - 1], g.gp[l - 1], g.gw[l - 1], g.gh[l - 1]}, base + g.off_l[l], g.gp[l]});
@@ -501,15 +524,16 @@ int Engine::wave_launch() {
   }
   int ndown = 0;
   for (int l = 1; l < kMaxLevels; l++) ndown += (int)down[l].size();
+  const int npyr = (int)pyr_.size();
   const int npairs = (int)wp_.size();
-  if (npairs == 0 && ndown == 0) return 0;
+  if (npairs == 0 && ndown == 0 && npyr == 0) return 0;
   if (up_pending_) {
     // frames copied on the copy stream must land before their pyramids
     cudaError_t we = cudaStreamWaitEvent(stream, ev_up_, 0);
     if (we) { status = ANALYSER_ERR_CUDA; message = "cudaStreamWaitEvent(upload)"; return status; }
     up_pending_ = false;
   }
-  if (ensure_capacity(npairs, ndown)) { status = ANALYSER_ERR_CUDA; return status; }
+  if (ensure_capacity(npairs, ndown, npyr)) { status = ANALYSER_ERR_CUDA; return status; }
 
   // ---- pair jobs, grouped by tile shape ---------------------------------------
   std::stable_sort(wp_.begin(), wp_.end(), [](const WavePair& x, const WavePair& y) {
@@ -605,8 +629,30 @@ int Engine::wave_launch() {
     e = cudaMemcpyAsync(d_djobs, h_djobs, sizeof(DownJob) * ndown, cudaMemcpyHostToDevice, stream);
     if (e) return fail(e, "cudaMemcpyAsync(pyramid jobs)");
   }
+  int pmaxw = 0, pmaxh = 0;
+  if (npyr) {
+    for (int i = 0; i < npyr; i++) {
+      h_pyjobs[i] = pyr_[i];
+      pmaxw = std::max(pmaxw, pyr_[i].w);
+      pmaxh = std::max(pmaxh, pyr_[i].h);
+    }
+    e = cudaMemcpyAsync(d_pyjobs, h_pyjobs, sizeof(PyrJob) * npyr, cudaMemcpyHostToDevice, stream);
+    if (e) return fail(e, "cudaMemcpyAsync(pyramid jobs)");
+  }
   const bool timed = p.time_kernels != 0;
-  if (timed && ndown) cudaEventRecord(ev_[0], stream);
+  if (timed && (ndown || npyr)) cudaEventRecord(ev_[0], stream);
+  if (npyr) {
+    e = launch_pyramid(d_pyjobs, npyr, pmaxw, pmaxh, stream);
+    if (e) return fail(e, "pyramid_kernel");
+    n_launches++;
+    n_pyr_launches++;
+    for (const PyrJob& j : pyr_) {
+      // read level 0 once, write levels 1-2 of the frame and both fields
+      double b = (double)j.w * j.h + (double)(j.w / 2) * (j.h / 2) + 2.0 * (j.w / 2) * (j.h / 4);
+      if (j.out[1]) b += (double)(j.w / 4) * (j.h / 4) + 2.0 * (j.w / 4) * (j.h / 8);
+      pyr_bytes += b;
+    }
+  }
   for (int l = 1; l < kMaxLevels; l++) {
     if (!dcount[l]) continue;
     e = launch_downsample(d_djobs + dstart[l], dcount[l], dmaxh[l], dmaxw[l], stream);
@@ -615,7 +661,7 @@ int Engine::wave_launch() {
     n_pyr_launches++;
     for (const DownJob& j : down[l]) pyr_bytes += 2.0 * (j.src.h / 2) * (double)(2 * (j.src.w / 2)) * 1.25;
   }
-  if (timed && ndown) cudaEventRecord(ev_[1], stream);
+  if (timed && (ndown || npyr)) cudaEventRecord(ev_[1], stream);
   if (timed && !groups.empty()) cudaEventRecord(ev_[2], stream);
   for (const Group& gr : groups) {
     PairBatch b;
@@ -664,12 +710,12 @@ int Engine::wave_launch() {
   e = cudaMemcpyAsync(h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, stream);
   if (e) return fail(e, "cudaMemcpyAsync(status)");
   fl_npairs_ = npairs;
-  fl_ndown_ = ndown;
+  fl_ndown_ = ndown + npyr;
   fl_vec_total_ = vec_total;
   fl_groups_ = !groups.empty();
   fl_t1_ = tw1;
   inflight_ = true;
-  return npairs + ndown;
+  return npairs + ndown + npyr;
 }
 
 int Engine::wave_complete() {

@@ -132,7 +132,7 @@ class Engine {
   bool autotune = true;
 
  private:
-  int ensure_capacity(int npairs, int ndown);
+  int ensure_capacity(int npairs, int ndown, int npyr);
   int run_alone(Clip* c);
   int setup_pair_job(const Clip& c, uint64_t key, PairJob& pj, int item_begin, unsigned long long* rec,
                      short2* vec);
@@ -157,11 +157,14 @@ class Engine {
   double fl_t1_ = 0.0;
   int sm_count = 0;
   // wave buffers
-  int cap_pairs = 0, cap_down = 0;
+  int cap_pairs = 0, cap_down = 0, cap_pyr = 0;
   PairJob* d_pjobs = nullptr;
   PairJob* h_pjobs = nullptr;
   DownJob* d_djobs = nullptr;
   DownJob* h_djobs = nullptr;
+  PyrJob* d_pyjobs = nullptr;
+  PyrJob* h_pyjobs = nullptr;
+  std::vector<PyrJob> pyr_;   // this wave's fused pyramid jobs
   unsigned long long* d_rec = nullptr;
   unsigned long long* h_rec = nullptr;
   short2* d_vec = nullptr;

@@ -49,6 +49,114 @@ __global__ void downsample_kernel(const DownJob* __restrict__ jobs) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// pyramid levels 1-2 of frames and fields in one pass over level 0
+// ---------------------------------------------------------------------------
+
+// (a + b + c + d + 2) >> 2 for the four 2x2 boxes of two 8-byte rows
+__device__ __forceinline__ uint32_t box4(unsigned long long A, unsigned long long C) {
+  const unsigned long long M = 0x00FF00FF00FF00FFull;
+  const unsigned long long s = (A & M) + ((A >> 8) & M) + (C & M) + ((C >> 8) & M) + 0x0002000200020002ull;
+  const unsigned long long q = (s >> 2) & M;
+  return __byte_perm((uint32_t)q, (uint32_t)(q >> 32), 0x6420);
+}
+
+// 8 output bytes (two words) from two 16-byte rows
+__device__ __forceinline__ uint2 box8(uint4 a, uint4 c) {
+  const unsigned long long A0 = ((unsigned long long)a.y << 32) | a.x, A1 = ((unsigned long long)a.w << 32) | a.z;
+  const unsigned long long C0 = ((unsigned long long)c.y << 32) | c.x, C1 = ((unsigned long long)c.w << 32) | c.z;
+  return make_uint2(box4(A0, C0), box4(A1, C1));
+}
+
+__device__ __forceinline__ uint32_t box4w(uint2 a, uint2 c) {
+  return box4(((unsigned long long)a.y << 32) | a.x, ((unsigned long long)c.y << 32) | c.x);
+}
+
+__device__ __forceinline__ int box_px(const uint8_t* r0, const uint8_t* r1, int x) {
+  return (r0[2 * x] + r0[2 * x + 1] + r1[2 * x] + r1[2 * x + 1] + 2) >> 2;
+}
+
+// A thread covers level-0 rows 8Y..8Y+7 and columns 16X..16X+15.
+__global__ void __launch_bounds__(128) pyramid_kernel(const PyrJob* __restrict__ jobs) {
+  const PyrJob jb = jobs[blockIdx.z];
+  const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int W = jb.w, H = jb.h, x0 = 16 * X, y0 = 8 * Y;
+  if (x0 >= W || y0 >= H) return;
+  const int w1 = W / 2, w2 = W / 4, h1 = H / 2, h2 = H / 4, g1 = H / 4, g2 = H / 8;   // frame / field sizes
+  const bool two = jb.out[1] != nullptr;
+  if (x0 + 16 <= W) {
+    uint4 r[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+      r[i] = (y0 + i < H) ? __ldg(reinterpret_cast<const uint4*>(jb.l0 + (size_t)(y0 + i) * jb.l0_pitch + x0))
+                          : make_uint4(0, 0, 0, 0);
+    uint2 f1[4], u1[2], l1[2];
+#pragma unroll
+    for (int k = 0; k < 4; k++) f1[k] = box8(r[2 * k], r[2 * k + 1]);
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      u1[j] = box8(r[4 * j], r[4 * j + 2]);
+      l1[j] = box8(r[4 * j + 1], r[4 * j + 3]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+      if (4 * Y + k < h1) *reinterpret_cast<uint2*>(jb.out[0] + (size_t)(4 * Y + k) * jb.pitch[0] + 8 * X) = f1[k];
+#pragma unroll
+    for (int j = 0; j < 2; j++)
+      if (2 * Y + j < g1) {
+        *reinterpret_cast<uint2*>(jb.out[2] + (size_t)(2 * Y + j) * jb.pitch[2] + 8 * X) = u1[j];
+        *reinterpret_cast<uint2*>(jb.out[4] + (size_t)(2 * Y + j) * jb.pitch[4] + 8 * X) = l1[j];
+      }
+    if (two) {
+#pragma unroll
+      for (int m = 0; m < 2; m++)
+        if (2 * Y + m < h2)
+          *reinterpret_cast<uint32_t*>(jb.out[1] + (size_t)(2 * Y + m) * jb.pitch[1] + 4 * X) = box4w(f1[2 * m], f1[2 * m + 1]);
+      if (Y < g2) {
+        *reinterpret_cast<uint32_t*>(jb.out[3] + (size_t)Y * jb.pitch[3] + 4 * X) = box4w(u1[0], u1[1]);
+        *reinterpret_cast<uint32_t*>(jb.out[5] + (size_t)Y * jb.pitch[5] + 4 * X) = box4w(l1[0], l1[1]);
+      }
+    }
+    return;
+  }
+  // ragged right edge: pixel by pixel, level 1 first, level 2 from the stored level 1
+  // (the same thread wrote the level-1 pixels it reads back)
+  const uint8_t* row[8];
+#pragma unroll
+  for (int i = 0; i < 8; i++) row[i] = jb.l0 + (size_t)min(y0 + i, H - 1) * jb.l0_pitch;
+  for (int x = x0 / 2; x < min(x0 / 2 + 8, w1); x++) {
+    for (int k = 0; k < 4; k++)
+      if (4 * Y + k < h1) jb.out[0][(size_t)(4 * Y + k) * jb.pitch[0] + x] = (uint8_t)box_px(row[2 * k], row[2 * k + 1], x);
+    for (int j = 0; j < 2; j++)
+      if (2 * Y + j < g1) {
+        jb.out[2][(size_t)(2 * Y + j) * jb.pitch[2] + x] = (uint8_t)box_px(row[4 * j], row[4 * j + 2], x);
+        jb.out[4][(size_t)(2 * Y + j) * jb.pitch[4] + x] = (uint8_t)box_px(row[4 * j + 1], row[4 * j + 3], x);
+      }
+  }
+  if (!two) return;
+  for (int x = x0 / 4; x < min(x0 / 4 + 4, w2); x++) {
+    for (int m = 0; m < 2; m++)
+      if (2 * Y + m < h2) {
+        const uint8_t* a = jb.out[0] + (size_t)(4 * Y + 2 * m) * jb.pitch[0];
+        jb.out[1][(size_t)(2 * Y + m) * jb.pitch[1] + x] = (uint8_t)box_px(a, a + jb.pitch[0], x);
+      }
+    if (Y < g2) {
+      const uint8_t* a = jb.out[2] + (size_t)(2 * Y) * jb.pitch[2];
+      jb.out[3][(size_t)Y * jb.pitch[3] + x] = (uint8_t)box_px(a, a + jb.pitch[2], x);
+      const uint8_t* b = jb.out[4] + (size_t)(2 * Y) * jb.pitch[4];
+      jb.out[5][(size_t)Y * jb.pitch[5] + x] = (uint8_t)box_px(b, b + jb.pitch[4], x);
+    }
+  }
+}
+
+cudaError_t launch_pyramid(const PyrJob* d_jobs, int njobs, int max_w, int max_h, cudaStream_t st) {
+  if (njobs <= 0) return cudaSuccess;
+  dim3 blk(32, 4);
+  dim3 grd(((max_w + 15) / 16 + blk.x - 1) / blk.x, ((max_h + 7) / 8 + blk.y - 1) / blk.y, njobs);
+  pyramid_kernel<<<grd, blk, 0, st>>>(d_jobs);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_downsample(const DownJob* d_jobs, int njobs, int max_dst_h, int max_dst_w, cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
   dim3 blk(32, 8);

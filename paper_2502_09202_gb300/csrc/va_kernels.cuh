@@ -23,6 +23,19 @@ struct DownJob {
   int dst_pitch;
 };
 
+// Levels 1 and 2 of a frame and of both its fields from one read of level 0
+// (rows 2y, 2y+1 -> frame level 1; rows 4y, 4y+2 -> upper field; 4y+1, 4y+3 ->
+// lower field; level 2 from the rounded level-1 values).  out[] = frame L1,
+// frame L2, upper L1, upper L2, lower L1, lower L2; the level-2 entries are
+// null when the pyramid has two levels.
+struct PyrJob {
+  const uint8_t* l0;
+  uint8_t* out[6];
+  int pitch[6];
+  int l0_pitch;
+  int w, h;   // level-0 size (h even)
+};
+
 // One pair measure: I against J (both views have the same dims per level).
 struct PairJob {
   Plane I[kMaxLevels];
@@ -53,6 +66,7 @@ struct PairBatch {
 };
 
 // Host launchers (defined in va_kernels.cu).
+cudaError_t launch_pyramid(const PyrJob* d_jobs, int njobs, int max_w, int max_h, cudaStream_t st);
 cudaError_t launch_downsample(const DownJob* d_jobs, int njobs, int max_dst_h, int max_dst_w,
                               cudaStream_t st);
 cudaError_t launch_pairs(const PairBatch& b, int tbx, int tby, int grid, cudaStream_t st);
