@@ -149,34 +149,38 @@ int analyser_push_frames(analyser* a, const uint8_t* luma, long long pitch_bytes
   if (nframes < 0 || (nframes > 0 && !luma) || pitch_bytes < a->clip.geo.W) return ANALYSER_ERR_INVALID_ARG;
   if (a->clip.external_l0) return fail(a, ANALYSER_ERR_STATE, "host and device pushes cannot be mixed");
   va::Engine& e = *a->eng;
-  // pipeline: copy a first chunk, then repeatedly launch a wave on what is
-  // resident, copy the next chunk into free slots while it runs, and complete it
+  // pipeline: keep every free slot of the window filled with copies in flight
+  // (chunks of frames, one event each); launch a wave whenever resident frames
+  // or requested pairs give work, and block on a copy only when nothing else
+  // can run, so that copies and kernels overlap
+  constexpr int kChunk = 16;
   int done = 0;
   int stall = 0;
-  // half a window per copy, so that one half can be copied while the other computes
-  const int chunk = a->clip.cap / 2 > 0 ? a->clip.cap / 2 : 1;
-  auto copy_next = [&]() -> int {
-    const int k = e.upload_host(&a->clip, luma + (size_t)done * a->clip.geo.H * pitch_bytes, pitch_bytes,
-                                std::min(nframes - done, chunk));
-    if (k < 0 || e.status) return -1;
-    done += k;
-    return k;
-  };
-  if (copy_next() < 0) return fail(a, e.status ? e.status : ANALYSER_ERR_CUDA, e.message);
-  while (done < nframes) {
+  for (;;) {
+    if (done < nframes) {
+      const int k = e.upload_async(&a->clip, luma + (size_t)done * a->clip.geo.H * pitch_bytes, pitch_bytes,
+                                   nframes - done, kChunk);
+      if (k < 0 || e.status) return fail(a, e.status ? e.status : ANALYSER_ERR_CUDA, e.message);
+      done += k;
+    }
+    if (e.poll_uploads(&a->clip, false) < 0) return fail(a, e.status ? e.status : ANALYSER_ERR_CUDA, e.message);
     const int launched = e.wave_launch();
     if (launched < 0 || e.status) return fail(a, e.status ? e.status : launched, e.message);
-    const int k = copy_next();
-    if (k < 0) return fail(a, e.status ? e.status : ANALYSER_ERR_CUDA, e.message);
     if (launched > 0) {
       const int rc = e.wave_complete();
       if (rc < 0 || e.status) return fail(a, e.status ? e.status : rc, e.message);
+      stall = 0;
+      continue;
     }
-    if (launched > 0 || k > 0) stall = 0;
-    else if (++stall > 2) return fail(a, ANALYSER_ERR_STATE, "frame window cannot advance");
+    if (!a->clip.up_chunks.empty()) {
+      if (e.poll_uploads(&a->clip, true) < 0) return fail(a, e.status ? e.status : ANALYSER_ERR_CUDA, e.message);
+      stall = 0;
+      continue;
+    }
+    if (done >= nframes) break;
+    if (++stall > 2) return fail(a, ANALYSER_ERR_STATE, "frame window cannot advance");
   }
-  // the caller may reuse its buffer once this returns
-  if (e.sync_uploads()) return fail(a, ANALYSER_ERR_CUDA, "cudaStreamSynchronize(copies)");
+  // every copy has completed: the caller may reuse its buffer
   return ANALYSER_OK;
 }
 

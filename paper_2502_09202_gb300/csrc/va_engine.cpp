@@ -107,15 +107,18 @@ void Geometry::init(int width, int height, int levels, bool own_l0) {
     fw[l] = fw[l - 1] / 2; fh[l] = fh[l - 1] / 2; fp[l] = round_up(std::max(fw[l], 4), 16);
     gw[l] = gw[l - 1] / 2; gh[l] = gh[l - 1] / 2; gp[l] = round_up(std::max(gw[l], 4), 16);
   }
+  // level 0 of the slots is one contiguous array of frames (H * fp[0] bytes
+  // apart), so a run of consecutive slots is a single copy target; the pyramid
+  // levels of a slot follow in a second array
+  l0_bytes = own_l0 ? (size_t)fh[0] * fp[0] : 0;
   size_t off = 0;
-  l0_bytes = own_l0 ? round_up_sz((size_t)fh[0] * fp[0] + 64, 256) : 0;
-  off = l0_bytes;
   for (int l = 1; l < L; l++) { off_f[l] = off; off += round_up_sz((size_t)fh[l] * fp[l] + 16, 256); }
   for (int l = 1; l < L; l++) { off_u[l] = off; off += round_up_sz((size_t)gh[l] * gp[l] + 16, 256); }
   for (int l = 1; l < L; l++) { off_l[l] = off; off += round_up_sz((size_t)gh[l] * gp[l] + 16, 256); }
-  // a whole number of level-0 rows, so that consecutive slots form one pitched 3D copy target
-  slot_bytes = own_l0 ? round_up_sz(off, (size_t)fp[0] * 4) : off;
+  slot_bytes = round_up_sz(off, 256);
 }
+
+size_t Geometry::l0_region(int cap) const { return l0_bytes ? round_up_sz((size_t)cap * l0_bytes + 64, 256) : 0; }
 
 Engine::Engine(const analyser_params& params) : p(params) {}
 
@@ -124,7 +127,11 @@ Engine::~Engine() {
   if (stream) cudaStreamSynchronize(stream);
   if (cstream) cudaStreamSynchronize(cstream);
   if (rstream) cudaStreamSynchronize(rstream);
-  for (Clip* c : clips) pool_free(c->d_ring);
+  for (Clip* c : clips) {
+    for (auto& u : c->up_chunks) pool_release_event(u.second);
+    c->up_chunks.clear();
+    pool_free(c->d_ring);
+  }
   pool_free(d_status);
   pool_free_host(h_status);
   pool_free(d_pjobs);
@@ -187,7 +194,7 @@ int Engine::init(std::string& why) {
   return ANALYSER_OK;
 }
 
-size_t Engine::ring_bytes(const Geometry& g, int cap) { return (size_t)cap * g.slot_bytes; }
+size_t Engine::ring_bytes(const Geometry& g, int cap) { return g.l0_region(cap) + (size_t)cap * g.slot_bytes; }
 
 int Engine::add_clip(Clip* c, std::string& why, bool enlist) {
   c->p = p;
@@ -206,8 +213,9 @@ int Engine::add_clip(Clip* c, std::string& why, bool enlist) {
     why = std::string("cudaMalloc(window): ") + cudaGetErrorString(e);
     return ANALYSER_ERR_OOM;
   }
+  c->pyr = c->d_ring + c->geo.l0_region(c->cap);
   for (int s = 0; s < c->cap; s++) {
-    c->l0[s] = c->d_ring + (size_t)s * c->geo.slot_bytes;
+    c->l0[s] = c->geo.l0_bytes ? c->d_ring + (size_t)s * c->geo.l0_bytes : nullptr;
     c->l0_pitch[s] = c->geo.fp[0];
   }
   const int nbx = c->geo.W / c->geo.B0, nby = c->geo.H / c->geo.B0;
@@ -224,6 +232,11 @@ int Engine::add_clip(Clip* c, std::string& why, bool enlist) {
 
 void Engine::remove_clip(Clip* c) {
   clips.erase(std::remove(clips.begin(), clips.end(), c), clips.end());
+  if (!c->up_chunks.empty()) {
+    cudaStreamSynchronize(cstream);
+    for (auto& u : c->up_chunks) pool_release_event(u.second);
+    c->up_chunks.clear();
+  }
   if (c->d_ring) {
     // the window returns to the cache: nothing queued may still read or write it
     cudaStreamSynchronize(stream);
@@ -237,25 +250,26 @@ void Engine::remove_clip(Clip* c) {
 int Engine::upload_host(Clip* c, const uint8_t* frames, long long pitch, int nframes) {
   const int k = std::min(nframes, free_slots(c));
   const Geometry& g = c->geo;
-  // one 3D copy per run of consecutive slots: frames are `H*pitch` apart in
-  // host memory and `slot_bytes` (a whole number of level-0 rows) apart in the ring
+  // one copy per run of consecutive slots: frames are H*pitch apart in host
+  // memory and H*fp[0] apart in the ring (linear when the pitches agree; the
+  // last row stops at W so that nothing beyond the caller's frames is read)
   int i = 0;
   while (i < k) {
     const int s0 = c->slot_of(c->pushed + i);
     const int run = std::min(k - i, c->cap - s0);
-    cudaMemcpy3DParms cp = {};
-    cp.srcPtr = make_cudaPitchedPtr(const_cast<uint8_t*>(frames + (size_t)i * g.H * pitch), (size_t)pitch, g.W, g.H);
-    cp.dstPtr = make_cudaPitchedPtr(c->d_ring + (size_t)s0 * g.slot_bytes, (size_t)g.fp[0], g.W, g.slot_bytes / g.fp[0]);
-    cp.extent = make_cudaExtent(g.W, g.H, run);
-    cp.kind = cudaMemcpyHostToDevice;
-    cudaError_t e = cudaMemcpy3DAsync(&cp, cstream);
+    const uint8_t* src = frames + (size_t)i * g.H * pitch;
+    uint8_t* dst = c->d_ring + (size_t)s0 * g.l0_bytes;
+    const size_t rows = (size_t)run * g.H;
+    cudaError_t e = pitch == g.fp[0]
+                        ? cudaMemcpyAsync(dst, src, (rows - 1) * (size_t)pitch + g.W, cudaMemcpyHostToDevice, cstream)
+                        : cudaMemcpy2DAsync(dst, g.fp[0], src, (size_t)pitch, g.W, rows, cudaMemcpyHostToDevice, cstream);
     if (e != cudaSuccess) {
       status = ANALYSER_ERR_CUDA;
-      message = std::string("cudaMemcpy3DAsync(frames): ") + cudaGetErrorString(e);
+      message = std::string("cudaMemcpyAsync(frames): ") + cudaGetErrorString(e);
       return -1;
     }
     for (int j = 0; j < run; j++) {
-      c->l0[s0 + j] = c->d_ring + (size_t)(s0 + j) * g.slot_bytes;
+      c->l0[s0 + j] = dst + (size_t)j * g.l0_bytes;
       c->l0_pitch[s0 + j] = g.fp[0];
     }
     i += run;
@@ -267,6 +281,62 @@ int Engine::upload_host(Clip* c, const uint8_t* frames, long long pitch, int nfr
   }
   c->pushed += k;
   return k;
+}
+
+int Engine::upload_async(Clip* c, const uint8_t* frames, long long pitch, int nframes, int chunk) {
+  const Geometry& g = c->geo;
+  const int k = std::min(nframes, free_slots(c));
+  int i = 0;
+  while (i < k) {
+    const int f0 = c->uploaded;
+    const int s0 = c->slot_of(f0);
+    const int run = std::min(std::min(k - i, chunk), c->cap - s0);
+    const uint8_t* src = frames + (size_t)i * g.H * pitch;
+    uint8_t* dst = c->d_ring + (size_t)s0 * g.l0_bytes;
+    const size_t rows = (size_t)run * g.H;
+    cudaError_t e = pitch == g.fp[0]
+                        ? cudaMemcpyAsync(dst, src, (rows - 1) * (size_t)pitch + g.W, cudaMemcpyHostToDevice, cstream)
+                        : cudaMemcpy2DAsync(dst, g.fp[0], src, (size_t)pitch, g.W, rows, cudaMemcpyHostToDevice, cstream);
+    cudaEvent_t ev = nullptr;
+    if (e == cudaSuccess) e = pool_event(&ev, false);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, cstream);
+    if (e != cudaSuccess) {
+      pool_release_event(ev);
+      status = ANALYSER_ERR_CUDA;
+      message = std::string("cudaMemcpyAsync(frames): ") + cudaGetErrorString(e);
+      return -1;
+    }
+    for (int j = 0; j < run; j++) {
+      c->l0[s0 + j] = dst + (size_t)j * g.l0_bytes;
+      c->l0_pitch[s0 + j] = g.fp[0];
+    }
+    c->uploaded += run;
+    c->up_chunks.push_back({c->uploaded, ev});
+    h2d_bytes += (long long)run * g.W * g.H;
+    i += run;
+  }
+  return k;
+}
+
+int Engine::poll_uploads(Clip* c, bool wait) {
+  const int before = c->pushed;
+  while (!c->up_chunks.empty()) {
+    cudaEvent_t ev = c->up_chunks.front().second;
+    cudaError_t e = wait && c->pushed == before ? cudaEventSynchronize(ev) : cudaEventQuery(ev);
+    if (e == cudaErrorNotReady) {
+      cudaGetLastError();
+      break;
+    }
+    if (e != cudaSuccess) {
+      status = ANALYSER_ERR_CUDA;
+      message = std::string("frame copy: ") + cudaGetErrorString(e);
+      return -1;
+    }
+    c->pushed = c->up_chunks.front().first;
+    pool_release_event(ev);
+    c->up_chunks.pop_front();
+  }
+  return c->pushed - before;
 }
 
 int Engine::attach_device(Clip* c, const uint8_t* frames, long long pitch, long long stride, int nframes) {
@@ -422,8 +492,8 @@ int Engine::setup_pair_job(const Clip& c, uint64_t key, PairJob& pj, int item_be
   const Geometry& g = c.geo;
   const int kind = key_kind(key), a = key_a(key), b = key_b(key);
   const int sa = c.slot_of(a), sb = c.slot_of(b);
-  const uint8_t* ra = c.d_ring + (size_t)sa * g.slot_bytes;
-  const uint8_t* rb = c.d_ring + (size_t)sb * g.slot_bytes;
+  const uint8_t* ra = c.pyr + (size_t)sa * g.slot_bytes;
+  const uint8_t* rb = c.pyr + (size_t)sb * g.slot_bytes;
   const uint8_t* la = c.l0[sa];
   const uint8_t* lb = c.l0[sb];
   const int pa = c.l0_pitch[sa], pb = c.l0_pitch[sb];
@@ -485,7 +555,7 @@ int Engine::wave_launch() {
     const Geometry& g = c->geo;
     for (int f = c->pyr_done; f < c->pushed; f++) {
       const int s = c->slot_of(f);
-      uint8_t* base = c->d_ring + (size_t)s * g.slot_bytes;
+      uint8_t* base = c->pyr + (size_t)s * g.slot_bytes;
       const uint8_t* l0 = c->l0[s];
       const int p0 = c->l0_pitch[s];
       if (g.L < 2) continue;
@@ -620,14 +690,17 @@ int Engine::wave_launch() {
   cudaError_t e;
   (void)why;
   if (npairs) {
-    e = cudaMemcpyAsync(d_pjobs, h_pjobs, sizeof(PairJob) * npairs, cudaMemcpyHostToDevice, stream);
-    if (e) return fail(e, "cudaMemcpyAsync(pair jobs)");
+    // descriptors are read from page-locked memory by a kernel, not queued on a copy engine
+    e = launch_copy_words(h_pjobs, d_pjobs, sizeof(PairJob) * npairs, stream);
+    if (e) return fail(e, "copy(pair jobs)");
+    n_launches++;
     e = cudaMemsetAsync(d_rec, 0, sizeof(unsigned long long) * kRecWords * npairs, stream);
     if (e) return fail(e, "cudaMemsetAsync(records)");
   }
   if (ndown) {
-    e = cudaMemcpyAsync(d_djobs, h_djobs, sizeof(DownJob) * ndown, cudaMemcpyHostToDevice, stream);
-    if (e) return fail(e, "cudaMemcpyAsync(pyramid jobs)");
+    e = launch_copy_words(h_djobs, d_djobs, sizeof(DownJob) * ndown, stream);
+    if (e) return fail(e, "copy(pyramid jobs)");
+    n_launches++;
   }
   int pmaxw = 0, pmaxh = 0;
   if (npyr) {
@@ -636,8 +709,9 @@ int Engine::wave_launch() {
       pmaxw = std::max(pmaxw, pyr_[i].w);
       pmaxh = std::max(pmaxh, pyr_[i].h);
     }
-    e = cudaMemcpyAsync(d_pyjobs, h_pyjobs, sizeof(PyrJob) * npyr, cudaMemcpyHostToDevice, stream);
-    if (e) return fail(e, "cudaMemcpyAsync(pyramid jobs)");
+    e = launch_copy_words(h_pyjobs, d_pyjobs, sizeof(PyrJob) * npyr, stream);
+    if (e) return fail(e, "copy(pyramid jobs)");
+    n_launches++;
   }
   const bool timed = p.time_kernels != 0;
   if (timed && (ndown || npyr)) cudaEventRecord(ev_[0], stream);
@@ -699,16 +773,18 @@ int Engine::wave_launch() {
   }
   if (timed && !groups.empty()) cudaEventRecord(ev_[3], stream);
   if (npairs) {
-    e = cudaMemcpyAsync(h_rec, d_rec, sizeof(unsigned long long) * kRecWords * npairs, cudaMemcpyDeviceToHost, stream);
-    if (e) return fail(e, "cudaMemcpyAsync(records)");
+    e = launch_copy_words(d_rec, h_rec, sizeof(unsigned long long) * kRecWords * npairs, stream);
+    if (e) return fail(e, "copy(records)");
+    n_launches++;
     if (vec_total) {
       h_vec.resize(vec_total);
       e = cudaMemcpyAsync(h_vec.data(), d_vec, sizeof(short2) * vec_total, cudaMemcpyDeviceToHost, stream);
       if (e) return fail(e, "cudaMemcpyAsync(motion)");
     }
   }
-  e = cudaMemcpyAsync(h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, stream);
-  if (e) return fail(e, "cudaMemcpyAsync(status)");
+  e = launch_copy_words(d_status, h_status, sizeof(int), stream);
+  if (e) return fail(e, "copy(status)");
+  n_launches++;
   fl_npairs_ = npairs;
   fl_ndown_ = ndown + npyr;
   fl_vec_total_ = vec_total;

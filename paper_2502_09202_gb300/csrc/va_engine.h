@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <algorithm>
+#include <deque>
 #include <memory>
 #include <string>
 #include <unordered_set>
@@ -25,9 +27,10 @@ struct Geometry {
   int fw[kMaxLevels], fh[kMaxLevels], fp[kMaxLevels];   // frame levels (fp[0] = ring pitch)
   int gw[kMaxLevels], gh[kMaxLevels], gp[kMaxLevels];   // field levels
   size_t off_f[kMaxLevels], off_u[kMaxLevels], off_l[kMaxLevels];  // offsets within a slot (levels >= 1)
-  size_t slot_bytes = 0;
-  size_t l0_bytes = 0;
+  size_t slot_bytes = 0;                 // pyramid levels >= 1 of one slot
+  size_t l0_bytes = 0;                   // level 0 of one slot (0 when frames stay in caller memory)
   void init(int width, int height, int levels, bool own_l0 = true);
+  size_t l0_region(int cap) const;       // bytes of the level-0 array of `cap` slots
 };
 
 // One clip being analysed.
@@ -39,12 +42,15 @@ struct Clip {
   int tbx = 8, tby = 4;              // tile of the pair kernel (autotuned per resolution)
   // device window
   int cap = 0;                       // slots
-  uint8_t* d_ring = nullptr;         // cap * slot_bytes
+  uint8_t* d_ring = nullptr;         // level-0 array, then cap * slot_bytes of pyramids
+  uint8_t* pyr = nullptr;            // start of the pyramid array
   std::vector<const uint8_t*> l0;    // level-0 frame of each slot
   std::vector<int> l0_pitch;
   bool external_l0 = false;          // slots point at caller device frames
   // progress
-  int pushed = 0;        // frames [0, pushed) delivered
+  int pushed = 0;        // frames [0, pushed) delivered (resident on the device)
+  int uploaded = 0;      // frames [0, uploaded) handed to the copy stream (>= pushed on the chunked path)
+  std::deque<std::pair<int, cudaEvent_t>> up_chunks;   // (end frame, completion event) of chunked copies
   int pyr_done = 0;      // frames [0, pyr_done) have pyramids
   int evicted = 0;       // frames [0, evicted) no longer resident
   int aon_next = 0;      // next always-on pair (t, t+1) not yet requested
@@ -68,7 +74,7 @@ struct Clip {
   std::vector<std::pair<uint64_t, std::vector<short2>>> vec_out_;
   bool done() const { return det.done(); }
   int slot_of(int f) const { return f % cap; }
-  size_t device_bytes() const { return (size_t)cap * geo.slot_bytes; }
+  size_t device_bytes() const { return geo.l0_region(cap) + (size_t)cap * geo.slot_bytes; }
 };
 
 // Results kept for the C ABI.
@@ -106,7 +112,15 @@ class Engine {
   int wave_launch();
   int wave_complete();
   bool wave_inflight() const { return inflight_; }
-  int free_slots(const Clip* c) const { return c->cap - (c->pushed - c->evicted); }
+  int free_slots(const Clip* c) const { return c->cap - (std::max(c->pushed, c->uploaded) - c->evicted); }
+  // Chunked host upload: copies up to `nframes` frames into free slots, `chunk`
+  // frames per copy, each copy with its own event; the frames count as pushed
+  // only once poll_uploads() has seen their copy complete, so waves never wait
+  // on the GPU for copies still in flight.  Returns frames issued or -1.
+  int upload_async(Clip* c, const uint8_t* frames, long long pitch, int nframes, int chunk);
+  // Marks completed chunks as pushed (blocking on the oldest one when `wait`);
+  // returns the number of frames that became resident or -1.
+  int poll_uploads(Clip* c, bool wait);
   int sync_uploads() { return cudaStreamSynchronize(cstream) == cudaSuccess ? 0 : ANALYSER_ERR_CUDA; }
 
   // stateless measure for tests and timing

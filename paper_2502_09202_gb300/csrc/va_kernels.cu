@@ -157,6 +157,26 @@ cudaError_t launch_pyramid(const PyrJob* d_jobs, int njobs, int max_w, int max_h
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// small transfers between device memory and page-locked host memory, done by
+// the SMs (the GPU addresses page-locked memory directly): per-wave descriptors
+// and results that must not queue behind bulk frame copies on the copy engines
+// ---------------------------------------------------------------------------
+
+__global__ void copy_words_kernel(const uint4* __restrict__ src, uint4* __restrict__ dst, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+cudaError_t launch_copy_words(const void* src, void* dst, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  const size_t n = (bytes + 15) / 16;
+  const size_t blocks = (n + 255) / 256;
+  copy_words_kernel<<<(unsigned)(blocks < 1024 ? blocks : 1024), 256, 0, st>>>(static_cast<const uint4*>(src),
+                                                                                static_cast<uint4*>(dst), n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_downsample(const DownJob* d_jobs, int njobs, int max_dst_h, int max_dst_w, cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
   dim3 blk(32, 8);

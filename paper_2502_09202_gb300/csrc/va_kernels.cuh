@@ -66,6 +66,9 @@ struct PairBatch {
 };
 
 // Host launchers (defined in va_kernels.cu).
+// Copies ceil(bytes/16) 16-byte words with a kernel; src and dst are 16-byte
+// aligned device or page-locked host buffers of at least that many words.
+cudaError_t launch_copy_words(const void* src, void* dst, size_t bytes, cudaStream_t st);
 cudaError_t launch_pyramid(const PyrJob* d_jobs, int njobs, int max_w, int max_h, cudaStream_t st);
 cudaError_t launch_downsample(const DownJob* d_jobs, int njobs, int max_dst_h, int max_dst_w,
                               cudaStream_t st);
