@@ -54,6 +54,23 @@ def job_throughput(world, frames_per_rank, ms_per_step):
     return world * frames_per_rank / (ms_per_step / 1000.0)
 
 
+def _h2d_gbs(pinned, device, nbytes=1 << 28):
+    """Host-to-device copy bandwidth from page-locked memory, measured now (context
+    for the end-to-end number: the frames of a step cross this link once)."""
+    import torch
+    src = pinned.view(-1)[:nbytes]
+    dst = torch.empty(src.numel(), dtype=torch.uint8, device=f"cuda:{device}")
+    st = torch.cuda.current_stream()
+    dst.copy_(src, non_blocking=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(4):
+        dst.copy_(src, non_blocking=True)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return 4 * src.numel() / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+
 def _spec():
     from paper_2502_09202_gb300 import synth
     return synth.config_interlaced()
@@ -406,6 +423,7 @@ def run_gpu(args):
     ms = e0.elapsed_time(e1) / args.steps
 
     # --- end to end through host buffers --------------------------------------------------
+    link_gbs = _h2d_gbs(pinned, local)
     for _ in range(max(1, args.warmup // 2)):
         one_step_host()
     barrier()
@@ -444,7 +462,8 @@ def run_gpu(args):
                    "window_frames": args.window, "pairs_per_step": profs[-1]["pairs"], "waves_per_step": profs[-1]["waves"],
                    "cuts": res["cuts"], "dissolves": res["dissolves"], "label": res["label"]},
         "e2e": {"value": e2e_value, "unit": "frames/s", "ms_per_step": ms_e2e,
-                "h2d_bytes_per_step": int(hprofs[-1]["h2d_bytes"]), "d2h_bytes_per_step": int(hprofs[-1]["d2h_bytes"])},
+                "h2d_bytes_per_step": int(hprofs[-1]["h2d_bytes"]), "d2h_bytes_per_step": int(hprofs[-1]["d2h_bytes"]),
+                "h2d_link_gbs": link_gbs},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": "pair_kernel", "achieved": achieved, "peak": sad_peak,
                      "unit": "T|a-b|/s", "frac": (achieved / sad_peak) if achieved else None,

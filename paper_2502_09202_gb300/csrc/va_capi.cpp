@@ -395,21 +395,42 @@ int server_step(server* s, int* active) {
     s->used += r.bytes;
     s->queue.pop_front();
   }
-  // top up every admitted clip's window
+  // top up every admitted clip's window with asynchronous chunked copies (at
+  // most step_frames new frames per clip and step, so that short clips arriving
+  // later are not queued behind long ones); frames join the analysis once their
+  // copy has landed, so the wave below overlaps the copies issued here
+  constexpr int kChunk = 16;
   for (auto& kv : s->reqs) {
     server::Req& r = kv.second;
     if (!r.admitted || r.done) continue;
     if (r.uploaded < r.nframes) {
       int n = r.nframes - r.uploaded;
       if (s->p.step_frames > 0 && n > s->p.step_frames) n = s->p.step_frames;
-      const int k = e.upload_host(r.clip.get(), r.frames + (size_t)r.uploaded * r.clip->geo.H * r.pitch, r.pitch, n);
+      const int k = e.upload_async(r.clip.get(), r.frames + (size_t)r.uploaded * r.clip->geo.H * r.pitch, r.pitch,
+                                   n, kChunk);
       if (k < 0) return fail_srv(s, e.status, e.message);
       r.uploaded += k;
     }
-    if (r.uploaded == r.nframes) r.clip->finished = true;
   }
-  const int rc = e.wave();
+  auto land = [&](bool wait) -> int {
+    bool waited = !wait;
+    for (auto& kv : s->reqs) {
+      server::Req& r = kv.second;
+      if (!r.admitted || r.done) continue;
+      const bool block = !waited && !r.clip->up_chunks.empty();
+      if (e.poll_uploads(r.clip.get(), block) < 0) return -1;
+      waited = waited || block;
+      if (r.clip->pushed == r.nframes) r.clip->finished = true;
+    }
+    return 0;
+  };
+  if (land(false)) return fail_srv(s, e.status, e.message);
+  int rc = e.wave();
   if (rc < 0 || e.status) return fail_srv(s, e.status ? e.status : rc, e.message);
+  bool in_flight = false;
+  for (auto& kv : s->reqs)
+    if (kv.second.admitted && !kv.second.done && !kv.second.clip->up_chunks.empty()) in_flight = true;
+  if (rc == 0 && in_flight && land(true)) return fail_srv(s, e.status, e.message);   // nothing to compute yet
   // retire finished clips
   int n_active = (int)s->queue.size();
   for (auto& kv : s->reqs) {
@@ -424,7 +445,7 @@ int server_step(server* s, int* active) {
       r.clip->store.map.clear();
     } else {
       n_active++;
-      if (rc == 0 && r.uploaded == r.nframes && r.clip->pending.empty())
+      if (rc == 0 && !in_flight && r.uploaded == r.nframes && r.clip->pushed == r.nframes && r.clip->pending.empty())
         return fail_srv(s, ANALYSER_ERR_STATE, "a served clip stalled");
     }
   }

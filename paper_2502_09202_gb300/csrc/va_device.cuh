@@ -162,12 +162,19 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
       }
     }
   }
+  // sum the four lanes' partials: every candidate's SAD over the block is below
+  // 2^16 (at most 256 pixels * 255), so two candidates share a 32-bit shuffle
+  // and their halves never carry into each other
+  uint32_t pk[13];
+#pragma unroll
+  for (int j = 0; j < 13; j++) {
+    const int c0 = 2 * j, c1 = 2 * j + 1;
+    pk[j] = acc[c0 % 5][c0 / 5] | (c1 < 25 ? acc[c1 % 5][c1 / 5] << 16 : 0u);
+  }
 #pragma unroll
   for (int off = 1; off <= 2; off <<= 1) {
 #pragma unroll
-    for (int a = 0; a < 5; a++)
-#pragma unroll
-      for (int d = 0; d < 5; d++) acc[a][d] += __shfl_xor_sync(0xFFFFFFFFu, acc[a][d], off);
+    for (int j = 0; j < 13; j++) pk[j] += __shfl_xor_sync(0xFFFFFFFFu, pk[j], off);
   }
   uint32_t best = 0xFFFFFFFFu;
   if (valid) {
@@ -180,10 +187,18 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
     for (int a = 0; a < 5; a++) kx[a] = (uint32_t)abs(cx + a - RR) * k1 + (uint32_t)a - 25u * (uint32_t)n1min;
 #pragma unroll
     for (int d = 0; d < 5; d++) ky[d] = (uint32_t)abs(cy + d - RR) * k1 + 5u * (uint32_t)d;
+    uint32_t key[25];
 #pragma unroll
     for (int d = 0; d < 5; d++)
 #pragma unroll
-      for (int a = 0; a < 5; a++) best = min(best, acc[a][d] * 256u + kx[a] + ky[d]);
+      for (int a = 0; a < 5; a++) {
+        const int c = d * 5 + a;
+        const uint32_t sad = (c & 1) ? pk[c >> 1] >> 16 : pk[c >> 1] & 0xFFFFu;
+        key[c] = sad * 256u + kx[a] + ky[d];
+      }
+#pragma unroll
+    for (int c = 0; c < 24; c += 2) best = __vimin3_u32(best, key[c], key[c + 1]);
+    best = min(best, key[24]);
   }
   const int r = (int)(best & 255u) % 25;
   if (valid && t == 0) {
@@ -395,7 +410,11 @@ __device__ __forceinline__ void sums_phase(const PairBatch& b, const PairJob& jb
       if (jb.vec) jb.vec[(size_t)by * nbx + bx] = make_short2((short)vx, (short)vy);
     }
   }
-  unsigned long long v[kRecWords] = {si, sj, sii, sjj, sij, sab, samm};
+  // warp sums fit 32 bits: a thread sums fewer than 2,000 pixels (about 100
+  // with the supported tiles) and at most one block's AMM term, and
+  // 32 * 2000 * 255^2 < 2^32, 32 * floor(sqrt(2 * 102^2) * 2^16) < 2^32 (102 px:
+  // the reach with coarse radius 24); the CTA and pair totals are 64-bit
+  uint32_t v[kRecWords] = {si, sj, sii, sjj, sij, sab, samm};
 #pragma unroll
   for (int k = 0; k < kRecWords; k++) {
 #pragma unroll

@@ -145,7 +145,6 @@ Engine::~Engine() {
   pool_free(d_vec);
   pool_free(d_cvec);
   for (cudaEvent_t& e : ev_) pool_release_event(e);
-  pool_release_event(ev_up_);
   pool_release_event(ev_chunk_);
   pool_release_event(ev_join_);
   pool_release_stream(rstream);
@@ -180,7 +179,6 @@ int Engine::init(std::string& why) {
   VA_CUDA_TRY(pool_stream(&rstream), why);
   VA_CUDA_TRY(pool_event(&ev_chunk_, false), why);
   VA_CUDA_TRY(pool_event(&ev_join_, false), why);
-  VA_CUDA_TRY(pool_event(&ev_up_, false), why);
   VA_CUDA_TRY(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, p.device), why);
   // Q(k) = floor(sqrt(k) * 2^16) for every k = vx^2 + vy^2 the search can produce
   int vmax = p.radius_coarse;
@@ -245,42 +243,6 @@ void Engine::remove_clip(Clip* c) {
     pool_free(c->d_ring);
     c->d_ring = nullptr;
   }
-}
-
-int Engine::upload_host(Clip* c, const uint8_t* frames, long long pitch, int nframes) {
-  const int k = std::min(nframes, free_slots(c));
-  const Geometry& g = c->geo;
-  // one copy per run of consecutive slots: frames are H*pitch apart in host
-  // memory and H*fp[0] apart in the ring (linear when the pitches agree; the
-  // last row stops at W so that nothing beyond the caller's frames is read)
-  int i = 0;
-  while (i < k) {
-    const int s0 = c->slot_of(c->pushed + i);
-    const int run = std::min(k - i, c->cap - s0);
-    const uint8_t* src = frames + (size_t)i * g.H * pitch;
-    uint8_t* dst = c->d_ring + (size_t)s0 * g.l0_bytes;
-    const size_t rows = (size_t)run * g.H;
-    cudaError_t e = pitch == g.fp[0]
-                        ? cudaMemcpyAsync(dst, src, (rows - 1) * (size_t)pitch + g.W, cudaMemcpyHostToDevice, cstream)
-                        : cudaMemcpy2DAsync(dst, g.fp[0], src, (size_t)pitch, g.W, rows, cudaMemcpyHostToDevice, cstream);
-    if (e != cudaSuccess) {
-      status = ANALYSER_ERR_CUDA;
-      message = std::string("cudaMemcpyAsync(frames): ") + cudaGetErrorString(e);
-      return -1;
-    }
-    for (int j = 0; j < run; j++) {
-      c->l0[s0 + j] = dst + (size_t)j * g.l0_bytes;
-      c->l0_pitch[s0 + j] = g.fp[0];
-    }
-    i += run;
-  }
-  h2d_bytes += (long long)k * g.W * g.H;
-  if (k > 0) {
-    cudaEventRecord(ev_up_, cstream);
-    up_pending_ = true;
-  }
-  c->pushed += k;
-  return k;
 }
 
 int Engine::upload_async(Clip* c, const uint8_t* frames, long long pitch, int nframes, int chunk) {
@@ -597,12 +559,6 @@ int Engine::wave_launch() {
   const int npyr = (int)pyr_.size();
   const int npairs = (int)wp_.size();
   if (npairs == 0 && ndown == 0 && npyr == 0) return 0;
-  if (up_pending_) {
-    // frames copied on the copy stream must land before their pyramids
-    cudaError_t we = cudaStreamWaitEvent(stream, ev_up_, 0);
-    if (we) { status = ANALYSER_ERR_CUDA; message = "cudaStreamWaitEvent(upload)"; return status; }
-    up_pending_ = false;
-  }
   if (ensure_capacity(npairs, ndown, npyr)) { status = ANALYSER_ERR_CUDA; return status; }
 
   // ---- pair jobs, grouped by tile shape ---------------------------------------

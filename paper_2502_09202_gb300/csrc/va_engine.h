@@ -99,7 +99,6 @@ class Engine {
   static size_t ring_bytes(const Geometry& g, int cap);
 
   // copy host frames into a clip's free slots; returns frames taken
-  int upload_host(Clip* c, const uint8_t* frames, long long pitch, int nframes);
   // reference device frames
   int attach_device(Clip* c, const uint8_t* frames, long long pitch, long long stride, int nframes);
 
@@ -121,7 +120,6 @@ class Engine {
   // Marks completed chunks as pushed (blocking on the oldest one when `wait`);
   // returns the number of frames that became resident or -1.
   int poll_uploads(Clip* c, bool wait);
-  int sync_uploads() { return cudaStreamSynchronize(cstream) == cudaSuccess ? 0 : ANALYSER_ERR_CUDA; }
 
   // stateless measure for tests and timing
   int measure_pairs(int width, int height, const uint8_t* frames, long long pitch, long long stride, int nframes,
@@ -157,12 +155,10 @@ class Engine {
   int* d_status = nullptr;
   int* h_status = nullptr;
   cudaEvent_t ev_[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t ev_up_ = nullptr;     // last frame copy
   cudaStream_t rstream = nullptr;   // refinement kernels of the split path
   cudaEvent_t ev_chunk_ = nullptr, ev_join_ = nullptr;
   short2* d_cvec = nullptr;         // coarse vectors between the split kernels
   size_t cap_cvec = 0;
-  bool up_pending_ = false;
   // wave in flight (between wave_launch and wave_complete)
   bool inflight_ = false;
   int fl_npairs_ = 0, fl_ndown_ = 0;
