@@ -154,6 +154,7 @@ int analyser_push_frames(analyser* a, const uint8_t* luma, long long pitch_bytes
   // or requested pairs give work, and block on a copy only when nothing else
   // can run, so that copies and kernels overlap
   constexpr int kChunk = 16;
+  constexpr int kMinWave = 64;   // new frames a wave waits for while copies stream in
   int done = 0;
   int stall = 0;
   for (;;) {
@@ -164,6 +165,12 @@ int analyser_push_frames(analyser* a, const uint8_t* luma, long long pitch_bytes
       done += k;
     }
     if (e.poll_uploads(&a->clip, false) < 0) return fail(a, e.status ? e.status : ANALYSER_ERR_CUDA, e.message);
+    // every wave costs a host round trip: while copies are still landing and
+    // the detectors ask for nothing, let a few chunks accumulate first
+    if (!a->clip.up_chunks.empty() && a->clip.pending.empty() && a->clip.pushed - a->clip.pyr_done < kMinWave) {
+      if (e.poll_uploads(&a->clip, true) < 0) return fail(a, e.status ? e.status : ANALYSER_ERR_CUDA, e.message);
+      continue;
+    }
     const int launched = e.wave_launch();
     if (launched < 0 || e.status) return fail(a, e.status ? e.status : launched, e.message);
     if (launched > 0) {

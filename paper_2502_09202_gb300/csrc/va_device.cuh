@@ -77,9 +77,10 @@ struct RefineWin<8> {
 // Refinement of every block of a tile at one pyramid level (block side S,
 // radius RR), candidates v = 2*parent + d, |d| <= RR (Sec. III.A, coarse to
 // fine block matching).  Four lanes own a block (lanes 4*bl .. 4*bl+3):
-//  - they copy the block's window of J into shared memory (cp.async, rows
-//    t, t+4, ...; clamp-to-edge loads where the window leaves the image
-//    horizontally, row indices clamped), so a level needs no CTA barrier;
+//  - they copy the block's window of J into shared memory (cp.async, the
+//    four lanes of a row together; clamp-to-edge loads where the window leaves
+//    the image horizontally, row indices clamped), so a level needs no CTA
+//    barrier;
 //  - lane t covers 4-pixel column t % (S/4) and row slice t / (S/4) of the
 //    block, keeps those I words in registers and slides down the window rows,
 //    feeding all 25 (dx, dy) candidates; the four partial sums are added with
@@ -115,16 +116,25 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
   uint32_t* const win = s_win + bl * kRefineWinWords;
 
   // ---- staging ----------------------------------------------------------------
+  // The block's four lanes copy each row together (lane t: words t and t + 4):
+  // a warp instruction reads 16 contiguous bytes per block and writes 32
+  // distinct banks.  A window leaving the image horizontally is read
+  // clamp-to-edge, each lane its own rows.
   if (valid) {
     const bool inside = xa >= 0 && xa + 4 * Wn::RW <= Jl.w;
+    if (inside) {
+      const uint8_t* src = Jl.p + xa + 4 * t;
+#pragma unroll 4
+      for (int r = 0; r < Wn::WR; r++) {
+        const uint8_t* row = src + (size_t)clampi(yw + r, 0, Jl.h - 1) * Jl.pitch;
+        cp_async4(win + r * Wn::RW + t, row);
+        if (Wn::RW > 4 && t < Wn::RW - 4) cp_async4(win + r * Wn::RW + 4 + t, row + 16);
+      }
+    } else {
 #pragma unroll
-    for (int k = 0; k < Wn::WR / 4; k++) {
-      const int r = t + 4 * k;
-      const uint8_t* row = Jl.p + (size_t)clampi(yw + r, 0, Jl.h - 1) * Jl.pitch;
-      if (inside) {
-#pragma unroll
-        for (int c = 0; c < Wn::RW; c++) cp_async4(win + r * Wn::RW + c, row + xa + 4 * c);
-      } else {
+      for (int k = 0; k < Wn::WR / 4; k++) {
+        const int r = t + 4 * k;
+        const uint8_t* row = Jl.p + (size_t)clampi(yw + r, 0, Jl.h - 1) * Jl.pitch;
 #pragma unroll
         for (int c = 0; c < Wn::RW; c++) win[r * Wn::RW + c] = load4_clamped(row, xa + 4 * c, Jl.w);
       }
