@@ -495,7 +495,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-frames", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--window", type=int, default=256, help="frames resident per clip")
+    ap.add_argument("--window", type=int, default=512, help="frames resident per clip (1.7 GB at 1080p)")
     ap.add_argument("--mode", default="clip", choices=["clip", "kernel", "batched", "served"])
     ap.add_argument("--clips", type=int, default=64)
     ap.add_argument("--requests", type=int, default=512)
