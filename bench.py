@@ -27,6 +27,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "interlaced-tff-1920x1080x1500@25fps"
+# dram__bytes_read.sum + dram__bytes_write.sum of coarse_kernel + refine_kernel for 16 frame
+# pairs of this workload (one ncu --set full capture of `--mode kernel --pairs 64`), per pair;
+# to be re-taken whenever either kernel changes
+PAIR_KERNEL_DRAM_BYTES_PER_PAIR = (2.235136e6 + 44.858368e6 + 0.159744e6) / 16
 METRIC = "frames/s at 1080p luma (full analysis: measures + decisions)"
 
 
@@ -467,7 +471,9 @@ def run_gpu(args):
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": "pair_kernel", "achieved": achieved, "peak": sad_peak,
                      "unit": "T|a-b|/s", "frac": (achieved / sad_peak) if achieved else None,
-                     "traffic": None, "launches_per_step": pair_launches / args.steps,
+                     "traffic": PAIR_KERNEL_DRAM_BYTES_PER_PAIR,
+                     "traffic_unit": "DRAM bytes per 1080p frame pair, coarse + refine kernels (ncu capture)",
+                     "launches_per_step": pair_launches / args.steps,
                      "kernel_ms_per_step": pair_ms / args.steps, "pyramid_ms_per_step": pyr_ms / args.steps,
                      "peak_source": "measured live: analyser_measure_sad_peak (vabsdiff4.add register loop)",
                      "hbm_peak_gbs": peaks.get("hbm_gbs")},
