@@ -101,52 +101,78 @@ def _gen_chunk(args):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons during the timed region: one
+    nvidia-smi process streams a sample every `period_ms`, each line is stamped
+    on arrival, and the summary keeps the samples inside the region marked by
+    window() (the nearest ones when the region is shorter than a few periods)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_ms: int = 10):
         self.index = index
-        self.samples = []
-        self._stop = threading.Event()
+        self.period_ms = period_ms
+        self.samples = []          # (host time, fields)
+        self.region = None
+        self._proc = None
         self._t = None
 
-    def _run(self):
-        while True:
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
-                for line in out.stdout.strip().splitlines():
-                    self.samples.append([x.strip() for x in line.split(",")])
-            except Exception:
-                pass
-            if self._stop.wait(0.1):
-                break
+    def _read(self):
+        for line in self._proc.stdout:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 3:
+                self.samples.append((time.perf_counter(), f))
 
     def __enter__(self):
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+        try:
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", str(self.period_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            t_end = time.perf_counter() + 2.0
+            while not self.samples and time.perf_counter() < t_end:   # streaming before the region starts
+                time.sleep(0.01)
+        except OSError:
+            self._proc = None
         return self
 
+    def window(self, t0: float, t1: float):
+        self.region = (t0, t1)
+
     def __exit__(self, *exc):
-        self._stop.set()
-        self._t.join(timeout=10)
+        if self._proc is not None:
+            time.sleep(2 * self.period_ms / 1000.0)
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self._proc.kill()
+            self._t.join(timeout=5)
 
     def summary(self):
-        if not self.samples:
+        samples = self.samples
+        if self.region and samples:
+            t0, t1 = self.region
+            inside = [s for s in samples if t0 <= s[0] <= t1]
+            if len(inside) < 3:   # short region: the samples nearest to it
+                mid = 0.5 * (t0 + t1)
+                inside = sorted(samples, key=lambda s: abs(s[0] - mid))[:3]
+            samples = inside
+        rows = [s[1] for s in samples]
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for s in self.samples:
+        for r in rows:
             for i, n in enumerate(names):
-                if len(s) > 5 + i and s[5 + i].lower().startswith("active"):
+                if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.samples)}
+                "reasons": sorted(reasons), "samples": len(rows), "period_ms": self.period_ms}
 
 
 def _peaks():
@@ -412,18 +438,20 @@ def run_gpu(args):
         one_step_device()
     stream = torch.cuda.current_stream()
     # --- device-resident timing ---------------------------------------------------------
-    barrier()
-    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     profs = []
-    with ClockSampler(local) as clk:
+    with ClockSampler(local) as clk:   # streaming before the barrier
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         e0.record(stream)
         for _ in range(args.steps):
             res, prof = one_step_device(time_kernels=1)
             profs.append(prof)
         e1.record(stream)
         torch.cuda.synchronize()
-    barrier()
+        clk.window(t0, time.perf_counter())
+        barrier()
     ms = e0.elapsed_time(e1) / args.steps
 
     # --- end to end through host buffers --------------------------------------------------

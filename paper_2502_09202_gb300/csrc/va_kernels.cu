@@ -77,7 +77,7 @@ __device__ __forceinline__ int box_px(const uint8_t* r0, const uint8_t* r1, int 
 }
 
 // A thread covers level-0 rows 8Y..8Y+7 and columns 16X..16X+15.
-__global__ void __launch_bounds__(128) pyramid_kernel(const PyrJob* __restrict__ jobs) {
+__global__ void __launch_bounds__(128, 10) pyramid_kernel(const PyrJob* __restrict__ jobs) {
   const PyrJob jb = jobs[blockIdx.z];
   const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y * blockDim.y + threadIdx.y;
   const int W = jb.w, H = jb.h, x0 = 16 * X, y0 = 8 * Y;
