@@ -52,6 +52,12 @@ extern "C" {
 #define ANALYSER_PAIR_FRAME 0       /* I = frame a, J = frame b */
 #define ANALYSER_PAIR_UPPER_LOWER 1 /* I = upper field of a, J = lower field of b */
 #define ANALYSER_PAIR_LOWER_UPPER 2 /* I = lower field of a, J = upper field of b */
+/* Same-parity field pairs: an extension for repeated-field detection in the
+ * spirit of Sec. III.C (the paper measures only v0, v1, v2).  Available through
+ * analyser_measure_pairs and analyser_measure_pair_noalloc; the detectors do
+ * not use them. */
+#define ANALYSER_PAIR_UPPER_UPPER 3 /* I = upper field of a, J = upper field of b */
+#define ANALYSER_PAIR_LOWER_LOWER 4 /* I = lower field of a, J = lower field of b */
 
 /*
  * Parameters.  The paper fixes none of the motion estimator's choices and none
@@ -193,11 +199,13 @@ void analyser_destroy(analyser* a);
 /*
  * Stateless measure of `npairs` pairs on DEVICE frames, for tests and kernel
  * timing: pair k compares frame ia[k] with frame ib[k] of `frames` (frame f at
- * frames + f*frame_stride_bytes) with pair kind kinds[k].  records receives
+ * frames + f*frame_stride_bytes) with pair kind kinds[k] (ANALYSER_PAIR_FRAME ..
+ * ANALYSER_PAIR_LOWER_LOWER; field kinds need an even height).  records receives
  * 7 int64 per pair (sum i, sum j, sum i^2, sum j^2, sum i*j, sum |i-j|, S_amm)
  * in HOST memory; motion (optional, HOST) receives the level-0 field of every
  * pair, nby*nbx (vx, vy) int16 each.  `stream` is a cudaStream_t (0 = default).
- * Allocates its pyramids and queues on the device for the duration of the call.
+ * Takes its pyramids and queues from the library's resource cache for the
+ * duration of the call.
  */
 int analyser_measure_pairs(const analyser_params* p, int width, int height, const uint8_t* frames,
                            long long pitch_bytes, long long frame_stride_bytes, int nframes,
@@ -208,7 +216,8 @@ int analyser_measure_pairs(const analyser_params* p, int width, int height, cons
  * One pair measure that allocates no device memory: the same record as
  * analyser_measure_pairs (7 int64 written to HOST memory `record`) for frames
  * a and b in DEVICE memory (pitch_bytes a multiple of 16, 16-byte aligned
- * pointers) and pair kind `kind`.  The paper has no counterpart; it exists for
+ * pointers) and pair kind `kind` (ANALYSER_PAIR_FRAME .. ANALYSER_PAIR_LOWER_LOWER).
+ * The paper has no counterpart; it exists for
  * callers embedded in a host application that reserves all device memory up
  * front and forbids cudaMalloc/cudaFree while it runs (an allocation could
  * fail against that reservation, and both calls synchronise the device).

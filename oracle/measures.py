@@ -2,10 +2,14 @@
 
 Test infrastructure only (see oracle/__init__.py).
 
-Pair kinds (the three ways the detectors pair frames, Sec. III.A and III.C):
-  FRAME (0)       I = frame a,            J = frame b
-  UPPER_LOWER (1) I = upper field of a,   J = lower field of b   (v0 = (1,t,t), v1 = (1,t,t+1))
-  LOWER_UPPER (2) I = lower field of a,   J = upper field of b   (v2 = (2,t,t+1))
+Pair kinds (the three ways the detectors pair frames, Sec. III.A and III.C, and
+the two same-parity field pairs, an extension for repeated-field detection in
+the spirit of Sec. III.C that the detectors do not use):
+  FRAME (0)        I = frame a,            J = frame b
+  UPPER_LOWER (1)  I = upper field of a,   J = lower field of b   (v0 = (1,t,t), v1 = (1,t,t+1))
+  LOWER_UPPER (2)  I = lower field of a,   J = upper field of b   (v2 = (2,t,t+1))
+  UPPER_UPPER (3)  I = upper field of a,   J = upper field of b
+  LOWER_LOWER (4)  I = lower field of a,   J = lower field of b
 The upper field is the even rows 0, 2, 4, ... of the frame; the lower field the odd rows.
 """
 from __future__ import annotations
@@ -18,7 +22,7 @@ import numpy as np
 
 from . import build as _build
 
-FRAME, UPPER_LOWER, LOWER_UPPER = 0, 1, 2
+FRAME, UPPER_LOWER, LOWER_UPPER, UPPER_UPPER, LOWER_LOWER = 0, 1, 2, 3, 4
 
 _lib = None
 
@@ -70,6 +74,10 @@ def pair_images(kind: int, fa: np.ndarray, fb: np.ndarray):
         return field(fa, "upper"), field(fb, "lower")
     if kind == LOWER_UPPER:
         return field(fa, "lower"), field(fb, "upper")
+    if kind == UPPER_UPPER:
+        return field(fa, "upper"), field(fb, "upper")
+    if kind == LOWER_LOWER:
+        return field(fa, "lower"), field(fb, "lower")
     raise ValueError(kind)
 
 

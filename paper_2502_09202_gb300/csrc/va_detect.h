@@ -14,7 +14,8 @@
 
 namespace va {
 
-enum PairKind { kFrame = 0, kUpperLower = 1, kLowerUpper = 2 };
+enum PairKind { kFrame = 0, kUpperLower = 1, kLowerUpper = 2, kUpperUpper = 3, kLowerLower = 4 };
+constexpr int kPairKinds = 5;
 
 inline uint64_t pair_key(int kind, int a, int b) {
   return ((uint64_t)kind << 60) | ((uint64_t)(uint32_t)a << 30) | (uint64_t)(uint32_t)b;

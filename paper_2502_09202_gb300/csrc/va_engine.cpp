@@ -469,13 +469,15 @@ int Engine::setup_pair_job(const Clip& c, uint64_t key, PairJob& pj, int item_be
     pj.nbx = g.W / g.B0;
     pj.nby = g.H / g.B0;
   } else {
-    const bool ul = kind == kUpperLower;
+    // which field of a is I and which field of b is J
+    const bool iu = kind == kUpperLower || kind == kUpperUpper;
+    const bool ju = kind == kLowerUpper || kind == kUpperUpper;
     // level-0 fields are row-strided views of the frames
-    pj.I[0] = {ul ? la : la + pa, 2 * pa, g.W, g.H / 2};
-    pj.J[0] = {ul ? lb + pb : lb, 2 * pb, g.W, g.H / 2};
+    pj.I[0] = {iu ? la : la + pa, 2 * pa, g.W, g.H / 2};
+    pj.J[0] = {ju ? lb : lb + pb, 2 * pb, g.W, g.H / 2};
     for (int l = 1; l < g.L; l++) {
-      pj.I[l] = {ra + (ul ? g.off_u[l] : g.off_l[l]), g.gp[l], g.gw[l], g.gh[l]};
-      pj.J[l] = {rb + (ul ? g.off_l[l] : g.off_u[l]), g.gp[l], g.gw[l], g.gh[l]};
+      pj.I[l] = {ra + (iu ? g.off_u[l] : g.off_l[l]), g.gp[l], g.gw[l], g.gh[l]};
+      pj.J[l] = {rb + (ju ? g.off_u[l] : g.off_l[l]), g.gp[l], g.gw[l], g.gh[l]};
     }
     pj.nbx = g.W / g.B0;
     pj.nby = (g.H / 2) / g.B0;
@@ -856,7 +858,7 @@ int Engine::measure_pairs(int width, int height, const uint8_t* frames, long lon
     return ANALYSER_ERR_INVALID_ARG;
   }
   for (int i = 0; i < npairs; i++) {
-    if (kinds[i] < 0 || kinds[i] > 2 || ia[i] < 0 || ib[i] < 0 || ia[i] >= nframes || ib[i] >= nframes) {
+    if (kinds[i] < 0 || kinds[i] >= kPairKinds || ia[i] < 0 || ib[i] < 0 || ia[i] >= nframes || ib[i] >= nframes) {
       why = "pair index or kind out of range";
       return ANALYSER_ERR_INVALID_ARG;
     }

@@ -75,7 +75,7 @@ extern "C" int analyser_measure_pair_noalloc(const analyser_params* p, int width
                                              int64_t* record, void* stream) {
   using namespace va;
   if (!p || !frame_a || !frame_b || !record) return ANALYSER_ERR_INVALID_ARG;
-  if (kind < 0 || kind > 2) return ANALYSER_ERR_INVALID_ARG;
+  if (kind < ANALYSER_PAIR_FRAME || kind > ANALYSER_PAIR_LOWER_LOWER) return ANALYSER_ERR_INVALID_ARG;
   if (width < 64 || height < 64 || (height & 1) || (long long)width * height > 11800000LL)
     return ANALYSER_ERR_INVALID_ARG;
   if (p->levels != 3 || p->block != 16 || p->radius_refine < 0 || p->radius_refine > 4 || p->mv_cost < 0 ||
@@ -88,8 +88,10 @@ extern "C" int analyser_measure_pair_noalloc(const analyser_params* p, int width
   const bool field = kind != ANALYSER_PAIR_FRAME;
   const int h0 = field ? height / 2 : height;
   const long long p0 = field ? 2 * pitch_bytes : pitch_bytes;
-  const uint8_t* I0 = kind == ANALYSER_PAIR_LOWER_UPPER ? frame_a + pitch_bytes : frame_a;
-  const uint8_t* J0 = kind == ANALYSER_PAIR_UPPER_LOWER ? frame_b + pitch_bytes : frame_b;
+  const bool i_lower = kind == ANALYSER_PAIR_LOWER_UPPER || kind == ANALYSER_PAIR_LOWER_LOWER;
+  const bool j_lower = kind == ANALYSER_PAIR_UPPER_LOWER || kind == ANALYSER_PAIR_LOWER_LOWER;
+  const uint8_t* I0 = i_lower ? frame_a + pitch_bytes : frame_a;
+  const uint8_t* J0 = j_lower ? frame_b + pitch_bytes : frame_b;
   const int w1 = width / 2, h1 = h0 / 2, w2 = w1 / 2, h2 = h1 / 2;
   const int p1 = round16(w1), p2 = round16(w2);
 

@@ -39,9 +39,9 @@ def test_measure_pairs_bit_exact_random_content(w, h):
     clip = synth.Clip(synth.ClipSpec(w, h, 6, 25.0, synth.TFF, 5, 3.0,
                                      synth.SceneStyle(n_objects=(4, 6), obj_speed=12, cell=8, bg_kind="textured")))
     frames = clip.frames()
-    kinds = [0, 0, 1, 1, 2, 0, 0]
-    ia = [0, 1, 2, 3, 4, 5, 0]
-    ib = [1, 2, 2, 4, 5, 0, 5]
+    kinds = [0, 0, 1, 1, 2, 0, 0, 3, 4]
+    ia = [0, 1, 2, 3, 4, 5, 0, 1, 2]
+    ib = [1, 2, 2, 4, 5, 0, 5, 2, 3]
     rec, mot = api.measure_pairs(_dev(frames), kinds, ia, ib, want_motion=True)
     for k in range(len(kinds)):
         ref, vec = _oracle_pair(kinds[k], frames[ia[k]], frames[ib[k]])
@@ -225,7 +225,7 @@ def test_split_and_fused_kernels_match_the_oracle(mode):
     clip = synth.Clip(synth.ClipSpec(w, h, 5, 25.0, synth.BFF, 9, 3.0,
                                      synth.SceneStyle(n_objects=(4, 6), obj_speed=10, cell=8, bg_kind="textured")))
     frames = clip.frames()
-    kinds, ia, ib = [0, 1, 2, 0, 0, 1], [0, 1, 2, 3, 4, 4], [1, 2, 3, 4, 0, 4]
+    kinds, ia, ib = [0, 1, 2, 0, 0, 1, 3, 4], [0, 1, 2, 3, 4, 4, 0, 3], [1, 2, 3, 4, 0, 4, 1, 4]
     rec, mot = api.measure_pairs(_dev(frames), kinds, ia, ib, want_motion=True, kernel_mode=mode)
     for k in range(len(kinds)):
         ref, vec = _oracle_pair(kinds[k], frames[ia[k]], frames[ib[k]])

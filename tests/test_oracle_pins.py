@@ -281,3 +281,21 @@ def test_field_kinds_pick_the_right_rows():
     assert np.array_equal(I, a[0::2]) and np.array_equal(J, b[1::2])
     I, J = M.pair_images(M.LOWER_UPPER, a, b)
     assert np.array_equal(I, a[1::2]) and np.array_equal(J, b[0::2])
+    I, J = M.pair_images(M.UPPER_UPPER, a, b)
+    assert np.array_equal(I, a[0::2]) and np.array_equal(J, b[0::2])
+    I, J = M.pair_images(M.LOWER_LOWER, a, b)
+    assert np.array_equal(I, a[1::2]) and np.array_equal(J, b[1::2])
+
+
+def test_same_parity_field_pair_of_a_repeated_field_is_static():
+    # a frame whose lower field repeats the previous frame's lower field: the
+    # lower-lower pair sees identical images (zero motion field, NCC 1, ACT 0)
+    # and the upper-upper pair does not; a repeated field is the cue the
+    # same-parity measure adds for 3:2 pulldown
+    rng = np.random.default_rng(5)
+    prev = rng.integers(0, 256, (96, 128), dtype=np.uint8)
+    cur = rng.integers(0, 256, (96, 128), dtype=np.uint8)
+    cur[1::2] = prev[1::2]
+    m = M.measure(M.LOWER_LOWER, prev, cur)
+    assert m["samm"] == 0 and m["ncc"] == 1.0 and m["act"] == 0.0
+    assert M.measure(M.UPPER_UPPER, prev, cur)["act"] > 0.0

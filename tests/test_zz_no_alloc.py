@@ -40,7 +40,7 @@ def test_noalloc_matches_measure_pairs_on_consecutive_calls():
     buf = _dev(frames)
     view = buf[:, :, :spec.width]
     p = N.default_params()
-    calls = [(0, 0, 1), (1, 2, 3), (2, 1, 2), (0, 3, 0)]
+    calls = [(0, 0, 1), (1, 2, 3), (2, 1, 2), (0, 3, 0), (3, 1, 2), (4, 0, 3)]
     want, _ = api.measure_pairs(view, [c[0] for c in calls], [c[1] for c in calls], [c[2] for c in calls])
     # two calls in a row (and two more): each equals the allocating entry point, exactly
     for k, (kind, a, b) in enumerate(calls):
