@@ -101,6 +101,7 @@ typedef struct {
   int kernel_mode;                     /* 0: split coarse / refine kernels on two streams for the default
                                           estimator (levels 3, radius_refine 2), fused otherwise;
                                           1: always the fused kernel (0) */
+  int want_histogram;                  /* per-frame luma histogram and its statistics (0) */
 } analyser_params;
 
 /* One measure of one pair, in the order of (kind, a, b). */
@@ -121,6 +122,22 @@ typedef struct {
   int analysed;        /* frames that voted */
 } analyser_shot;
 
+/*
+ * Unary measure of one frame (Sec. III.A lists histogram measures among the
+ * unary ones; this is their exact integer form): the 256-bin histogram of the
+ * level-0 luma and statistics derived from it.  With n = width*height,
+ * S1 = sum v, S2 = sum v^2 (exact integers): mean = S1 / n,
+ * std = sqrt((n*S2 - S1^2) / (n*n)) in FP64 with that operation order,
+ * median = lower median of the values (sorted index (n-1)/2) and mad = lower
+ * median of |v - median|.  Not used by the detectors.
+ */
+typedef struct {
+  int frame;
+  uint32_t bins[256];
+  double mean, std;
+  int median, mad;
+} analyser_frame_hist;
+
 typedef struct {
   int nframes;
   int ncuts;      const int* cuts;            /* first frame of each new shot after a hardcut */
@@ -131,6 +148,7 @@ typedef struct {
   int nmeasures;  const analyser_measure* measures;
   int motion_w, motion_h;                     /* block grid of the motion dumps (0 if none) */
   const int16_t* motion;                      /* (nframes-1) x motion_h x motion_w x 2 (vx, vy), or null */
+  int nhist;      const analyser_frame_hist* hist;   /* one per frame when params.want_histogram, else 0 */
 } analyser_results_t;
 
 typedef struct analyser analyser;

@@ -186,3 +186,30 @@ def finalise(r: dict) -> dict:
 def measure(kind: int, fa: np.ndarray, fb: np.ndarray, sp: SearchParams = SearchParams()) -> dict:
     I, J = pair_images(kind, fa, fb)
     return finalise(pair_record(I, J, sp))
+
+
+def frame_histogram(frame: np.ndarray) -> dict:
+    """Unary measure of a frame (Sec. III.A names histogram measures among the
+    unary ones): the 256-bin histogram of its luma and statistics from exact
+    integer sums S1 = sum v, S2 = sum v^2 over the n pixels:
+    mean = S1/n, std = sqrt((n*S2 - S1^2) / (n*n)) (FP64, this order),
+    median = lower median (sorted index (n-1)//2), mad = lower median of
+    |v - median|."""
+    f = np.asarray(frame, dtype=np.uint8)
+    bins = np.bincount(f.ravel(), minlength=256).astype(np.int64)
+    n = int(f.size)
+    v = np.arange(256, dtype=np.int64)
+    s1 = int((v * bins).sum())
+    s2 = int((v * v * bins).sum())
+    mean = float(s1) / float(n)
+    std = math.sqrt(float(n * s2 - s1 * s1) / (float(n) * float(n)))
+    k = (n - 1) // 2
+    med = int(np.searchsorted(np.cumsum(bins), k + 1))
+    dev = np.zeros(256, dtype=np.int64)
+    for d in range(256):
+        if d == 0:
+            dev[d] = bins[med]
+        else:
+            dev[d] = (bins[med + d] if med + d < 256 else 0) + (bins[med - d] if med - d >= 0 else 0)
+    mad = int(np.searchsorted(np.cumsum(dev), k + 1))
+    return {"bins": bins, "mean": mean, "std": std, "median": med, "mad": mad}

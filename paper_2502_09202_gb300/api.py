@@ -81,6 +81,10 @@ def results_to_dict(r: N.Results) -> dict:
     if r.motion:
         n = max(r.nframes - 1, 0) * r.motion_h * r.motion_w * 2
         out["motion"] = np.ctypeslib.as_array(r.motion, shape=(n,)).reshape(-1, r.motion_h, r.motion_w, 2).copy()
+    if r.nhist > 0:
+        h = np.ctypeslib.as_array(r.hist, shape=(r.nhist,)).copy()
+        out["histograms"] = [{"frame": int(x["frame"]), "bins": x["bins"].astype(np.int64), "mean": float(x["mean"]),
+                              "std": float(x["std"]), "median": int(x["median"]), "mad": int(x["mad"])} for x in h]
     return out
 
 

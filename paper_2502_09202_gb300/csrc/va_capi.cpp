@@ -109,6 +109,7 @@ int analyser_default_params(analyser_params* p) {
   p->time_kernels = 0;
   p->step_frames = 32;
   p->kernel_mode = 0;
+  p->want_histogram = 0;
   return ANALYSER_OK;
 }
 

@@ -3,6 +3,7 @@
 #include "va_pool.h"
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <cstring>
 #include <map>
@@ -47,6 +48,37 @@ static void build_qtab(uint32_t* q, int qmax) {
   for (int k = 0; k <= qmax; k++) q[k] = (uint32_t)isqrt_digits((uint64_t)k << 32);
 }
 
+// Statistics of a frame's 256-bin histogram (n pixels): exact integer sums
+// S1, S2, then mean = S1/n and std = sqrt((n*S2 - S1^2) / (n*n)) in FP64 with
+// that operation order; lower median and lower median of |v - median|.
+static void hist_stats(const uint32_t* bins, int64_t n, analyser_frame_hist& h) {
+  int64_t s1 = 0, s2 = 0;
+  for (int v = 0; v < 256; v++) {
+    h.bins[v] = bins[v];
+    s1 += (int64_t)v * bins[v];
+    s2 += (int64_t)v * v * bins[v];
+  }
+  h.mean = (double)s1 / (double)n;
+  h.std = std::sqrt((double)(n * s2 - s1 * s1) / ((double)n * (double)n));
+  const int64_t k = (n - 1) / 2;   // index of the lower median in sorted order
+  int64_t c = 0;
+  int med = 255;
+  for (int v = 0; v < 256; v++) {
+    c += bins[v];
+    if (c > k) { med = v; break; }
+  }
+  c = 0;
+  int mad = 255;
+  for (int d = 0; d < 256; d++) {
+    const int64_t cnt = d == 0 ? bins[med]
+                               : (int64_t)(med + d < 256 ? bins[med + d] : 0) + (med - d >= 0 ? bins[med - d] : 0);
+    c += cnt;
+    if (c > k) { mad = d; break; }
+  }
+  h.median = med;
+  h.mad = mad;
+}
+
 int validate_params(const analyser_params& p, std::string& why) {
   if (p.levels < 2 || p.levels > 3) { why = "levels must be 2 or 3"; return ANALYSER_ERR_INVALID_ARG; }
   if (p.block != (kCoarseSide << (p.levels - 1))) {
@@ -71,6 +103,10 @@ int validate_params(const analyser_params& p, std::string& why) {
   }
   if ((p.tile_x || p.tile_y) && !pair_tile_supported(p.radius_coarse, p.tile_x, p.tile_y)) {
     why = "tile_x x tile_y is not a compiled tile shape";
+    return ANALYSER_ERR_INVALID_ARG;
+  }
+  if (p.want_histogram < 0 || p.want_histogram > 1) {
+    why = "want_histogram must be 0 or 1";
     return ANALYSER_ERR_INVALID_ARG;
   }
   if (p.kernel_mode < 0 || p.kernel_mode > 1) {
@@ -131,6 +167,7 @@ Engine::~Engine() {
     for (auto& u : c->up_chunks) pool_release_event(u.second);
     c->up_chunks.clear();
     pool_free(c->d_ring);
+    pool_free(c->d_hist);
   }
   pool_free(d_status);
   pool_free_host(h_status);
@@ -140,6 +177,7 @@ Engine::~Engine() {
   pool_free_host(h_djobs);
   pool_free(d_pyjobs);
   pool_free_host(h_pyjobs);
+  pool_free_host(h_hist);
   pool_free(d_rec);
   pool_free_host(h_rec);
   pool_free(d_vec);
@@ -211,6 +249,15 @@ int Engine::add_clip(Clip* c, std::string& why, bool enlist) {
     why = std::string("cudaMalloc(window): ") + cudaGetErrorString(e);
     return ANALYSER_ERR_OOM;
   }
+  if (p.want_histogram && !c->stateless_) {
+    e = pool_malloc(reinterpret_cast<void**>(&c->d_hist), sizeof(uint32_t) * 256 * c->cap);
+    if (e != cudaSuccess) {
+      pool_free(c->d_ring);
+      c->d_ring = nullptr;
+      why = std::string("cudaMalloc(histograms): ") + cudaGetErrorString(e);
+      return ANALYSER_ERR_OOM;
+    }
+  }
   c->pyr = c->d_ring + c->geo.l0_region(c->cap);
   for (int s = 0; s < c->cap; s++) {
     c->l0[s] = c->geo.l0_bytes ? c->d_ring + (size_t)s * c->geo.l0_bytes : nullptr;
@@ -242,6 +289,8 @@ void Engine::remove_clip(Clip* c) {
     cudaStreamSynchronize(rstream);
     pool_free(c->d_ring);
     c->d_ring = nullptr;
+    pool_free(c->d_hist);
+    c->d_hist = nullptr;
   }
 }
 
@@ -514,6 +563,8 @@ int Engine::wave_launch() {
   // ---- gather ---------------------------------------------------------------
   std::vector<DownJob> down[kMaxLevels];
   pyr_.clear();
+  hist_runs_.clear();
+  int nhist = 0;
   for (Clip* c : clips) {
     if (c->status || c->done()) continue;
     const Geometry& g = c->geo;
@@ -536,6 +587,14 @@ int Engine::wave_launch() {
       pj.out[1] = two ? base + g.off_f[2] : nullptr; pj.pitch[1] = two ? g.fp[2] : 0;
       pj.out[3] = two ? base + g.off_u[2] : nullptr; pj.pitch[3] = two ? g.gp[2] : 0;
       pj.out[5] = two ? base + g.off_l[2] : nullptr; pj.pitch[5] = two ? g.gp[2] : 0;
+      pj.hist = nullptr;
+      if (c->d_hist) {
+        pj.hist = c->d_hist + (size_t)256 * s;
+        HistRun* last = hist_runs_.empty() ? nullptr : &hist_runs_.back();
+        if (last && last->clip == c && last->frame0 + last->n == f && last->slot0 + last->n == s) last->n++;
+        else hist_runs_.push_back({c, f, s, 1, nhist});
+        nhist++;
+      }
       pyr_.push_back(pj);
       for (int l = 3; l < g.L; l++) {
         down[l].push_back({{base + g.off_f[l - 1], g.fp[l - 1], g.fw[l - 1], g.fh[l - 1]}, base + g.off_f[l], g.fp[l]});
@@ -671,13 +730,32 @@ int Engine::wave_launch() {
     if (e) return fail(e, "copy(pyramid jobs)");
     n_launches++;
   }
+  // per-frame histograms: zero the new frames' bins (one run of consecutive slots at a time)
+  if (nhist > cap_hist) {
+    pool_free_host(h_hist);
+    h_hist = nullptr;
+    cap_hist = 0;
+    e = pool_malloc_host(reinterpret_cast<void**>(&h_hist), sizeof(uint32_t) * 256 * std::max(nhist, 64));
+    if (e) return fail(e, "cudaMallocHost(histograms)");
+    cap_hist = std::max(nhist, 64);
+  }
+  for (const HistRun& r : hist_runs_) {
+    e = cudaMemsetAsync(r.clip->d_hist + (size_t)256 * r.slot0, 0, sizeof(uint32_t) * 256 * r.n, stream);
+    if (e) return fail(e, "cudaMemsetAsync(histograms)");
+  }
   const bool timed = p.time_kernels != 0;
   if (timed && (ndown || npyr)) cudaEventRecord(ev_[0], stream);
   if (npyr) {
-    e = launch_pyramid(d_pyjobs, npyr, pmaxw, pmaxh, stream);
+    e = launch_pyramid(d_pyjobs, npyr, pmaxw, pmaxh, nhist > 0, stream);
     if (e) return fail(e, "pyramid_kernel");
-    n_launches++;
+    n_launches += nhist > 0 ? 2 : 1;
     n_pyr_launches++;
+    for (const HistRun& r : hist_runs_) {
+      e = launch_copy_words(r.clip->d_hist + (size_t)256 * r.slot0, h_hist + (size_t)256 * r.off,
+                            sizeof(uint32_t) * 256 * r.n, stream);
+      if (e) return fail(e, "copy(histograms)");
+      n_launches++;
+    }
     for (const PyrJob& j : pyr_) {
       // read level 0 once, write levels 1-2 of the frame and both fields
       double b = (double)j.w * j.h + (double)(j.w / 2) * (j.h / 2) + 2.0 * (j.w / 2) * (j.h / 4);
@@ -827,6 +905,16 @@ int Engine::wave_complete() {
       }
     }
   }
+  // ---- per-frame histograms ---------------------------------------------------------------
+  for (const HistRun& r : hist_runs_) {
+    Clip* c = r.clip;
+    if ((int)c->hist.size() < r.frame0 + r.n) c->hist.resize(r.frame0 + r.n);
+    for (int i = 0; i < r.n; i++) {
+      analyser_frame_hist& h = c->hist[r.frame0 + i];
+      h.frame = r.frame0 + i;
+      hist_stats(h_hist + (size_t)256 * (r.off + i), (int64_t)c->geo.W * c->geo.H, h);
+    }
+  }
   // ---- detectors and eviction ---------------------------------------------------------
   for (Clip* c : clips) {
     if (c->status || c->stateless_ || c->done()) continue;
@@ -951,6 +1039,9 @@ void build_results(const Clip& c, ResultsBuf& out) {
     r.motion_h = c.geo.H / c.geo.B0;
     r.motion = out.motion.data();
   }
+  out.hist = c.hist;
+  r.nhist = (int)out.hist.size();
+  r.hist = out.hist.empty() ? nullptr : out.hist.data();
 }
 
 }  // namespace va

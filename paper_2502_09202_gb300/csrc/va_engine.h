@@ -43,6 +43,7 @@ struct Clip {
   // device window
   int cap = 0;                       // slots
   uint8_t* d_ring = nullptr;         // level-0 array, then cap * slot_bytes of pyramids
+  uint32_t* d_hist = nullptr;        // cap * 256 bins of the slots' level-0 histograms (want_histogram)
   uint8_t* pyr = nullptr;            // start of the pyramid array
   std::vector<const uint8_t*> l0;    // level-0 frame of each slot
   std::vector<int> l0_pitch;
@@ -60,6 +61,7 @@ struct Clip {
   std::vector<uint64_t> pending;     // requests for the next wave
   std::unordered_set<uint64_t> inflight;
   std::vector<int16_t> motion;       // level-0 fields of (t, t+1) when want_motion
+  std::vector<analyser_frame_hist> hist;   // per frame when want_histogram
   int status = ANALYSER_OK;
   std::string message;
   // host frame source (server path)
@@ -83,6 +85,7 @@ struct ResultsBuf {
   std::vector<analyser_shot> shots;
   std::vector<analyser_measure> measures;
   std::vector<int16_t> motion;
+  std::vector<analyser_frame_hist> hist;
   analyser_results_t r{};
 };
 void build_results(const Clip& c, ResultsBuf& out);
@@ -174,6 +177,10 @@ class Engine {
   DownJob* h_djobs = nullptr;
   PyrJob* d_pyjobs = nullptr;
   PyrJob* h_pyjobs = nullptr;
+  uint32_t* h_hist = nullptr;        // page-locked bins of a wave's new frames
+  int cap_hist = 0;
+  struct HistRun { Clip* clip; int frame0, slot0, n, off; };   // n consecutive frames/slots at row `off` of h_hist
+  std::vector<HistRun> hist_runs_;
   std::vector<PyrJob> pyr_;   // this wave's fused pyramid jobs
   unsigned long long* d_rec = nullptr;
   unsigned long long* h_rec = nullptr;

@@ -77,9 +77,7 @@ __device__ __forceinline__ int box_px(const uint8_t* r0, const uint8_t* r1, int 
 }
 
 // A thread covers level-0 rows 8Y..8Y+7 and columns 16X..16X+15.
-__global__ void __launch_bounds__(128, 10) pyramid_kernel(const PyrJob* __restrict__ jobs) {
-  const PyrJob jb = jobs[blockIdx.z];
-  const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void pyramid_tile(const PyrJob& jb, int X, int Y) {
   const int W = jb.w, H = jb.h, x0 = 16 * X, y0 = 8 * Y;
   if (x0 >= W || y0 >= H) return;
   const int w1 = W / 2, w2 = W / 4, h1 = H / 2, h2 = H / 4, g1 = H / 4, g2 = H / 8;   // frame / field sizes
@@ -149,11 +147,52 @@ __global__ void __launch_bounds__(128, 10) pyramid_kernel(const PyrJob* __restri
   }
 }
 
-cudaError_t launch_pyramid(const PyrJob* d_jobs, int njobs, int max_w, int max_h, cudaStream_t st) {
+// The 256-bin histogram of the thread's level-0 pixels, added into the CTA's
+// shared bins and then into the frame's bins.  Called by every thread.
+__device__ __forceinline__ void histogram_tile(const PyrJob& jb, int X, int Y, uint32_t* s_hist, int tid) {
+  for (int i = tid; i < 256; i += 128) s_hist[i] = 0;
+  __syncthreads();
+  const int W = jb.w, H = jb.h, x0 = 16 * X, y0 = 8 * Y;
+  if (x0 < W && y0 < H) {
+    const int nx = min(16, W - x0);
+    for (int i = 0; i < 8 && y0 + i < H; i++) {
+      const uint8_t* row = jb.l0 + (size_t)(y0 + i) * jb.l0_pitch + x0;
+      if (nx == 16) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(row));
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 16; k++) atomicAdd(&s_hist[(w[k >> 2] >> (8 * (k & 3))) & 255u], 1u);
+      } else {
+        for (int k = 0; k < nx; k++) atomicAdd(&s_hist[row[k]], 1u);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < 256; i += 128)
+    if (s_hist[i]) atomicAdd(&jb.hist[i], s_hist[i]);
+}
+
+__global__ void __launch_bounds__(128, 10) pyramid_kernel(const PyrJob* __restrict__ jobs) {
+  const PyrJob jb = jobs[blockIdx.z];
+  pyramid_tile(jb, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+}
+
+// Per-frame level-0 histograms of the jobs whose `hist` is set (same grid as
+// pyramid_kernel; launched only when histograms are wanted).
+__global__ void __launch_bounds__(128) histogram_kernel(const PyrJob* __restrict__ jobs) {
+  __shared__ uint32_t s_hist[256];
+  const PyrJob& jb = jobs[blockIdx.z];
+  if (!jb.hist) return;   // CTA-uniform
+  histogram_tile(jb, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y, s_hist,
+                 threadIdx.y * blockDim.x + threadIdx.x);
+}
+
+cudaError_t launch_pyramid(const PyrJob* d_jobs, int njobs, int max_w, int max_h, bool histograms, cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
   dim3 blk(32, 4);
   dim3 grd(((max_w + 15) / 16 + blk.x - 1) / blk.x, ((max_h + 7) / 8 + blk.y - 1) / blk.y, njobs);
   pyramid_kernel<<<grd, blk, 0, st>>>(d_jobs);
+  if (histograms) histogram_kernel<<<grd, blk, 0, st>>>(d_jobs);
   return cudaGetLastError();
 }
 

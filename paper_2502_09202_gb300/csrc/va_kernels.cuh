@@ -33,7 +33,8 @@ struct PyrJob {
   uint8_t* out[6];
   int pitch[6];
   int l0_pitch;
-  int w, h;   // level-0 size (h even)
+  int w, h;         // level-0 size (h even)
+  uint32_t* hist;   // 256 bins the frame's level-0 values are added to, or null
 };
 
 // One pair measure: I against J (both views have the same dims per level).
@@ -69,7 +70,8 @@ struct PairBatch {
 // Copies ceil(bytes/16) 16-byte words with a kernel; src and dst are 16-byte
 // aligned device or page-locked host buffers of at least that many words.
 cudaError_t launch_copy_words(const void* src, void* dst, size_t bytes, cudaStream_t st);
-cudaError_t launch_pyramid(const PyrJob* d_jobs, int njobs, int max_w, int max_h, cudaStream_t st);
+// pyramid_kernel, then histogram_kernel when `histograms` (jobs with hist set)
+cudaError_t launch_pyramid(const PyrJob* d_jobs, int njobs, int max_w, int max_h, bool histograms, cudaStream_t st);
 cudaError_t launch_downsample(const DownJob* d_jobs, int njobs, int max_dst_h, int max_dst_w,
                               cudaStream_t st);
 cudaError_t launch_pairs(const PairBatch& b, int tbx, int tby, int grid, cudaStream_t st);

@@ -32,7 +32,7 @@ class Params(ctypes.Structure):
         ("kf_theta", c_double),
         ("device", c_int), ("window_frames", c_int), ("mem_budget_bytes", c_ull), ("want_motion", c_int),
         ("tile_x", c_int), ("tile_y", c_int), ("time_kernels", c_int),
-        ("step_frames", c_int), ("kernel_mode", c_int),
+        ("step_frames", c_int), ("kernel_mode", c_int), ("want_histogram", c_int),
     ]
 
 
@@ -48,6 +48,11 @@ class Shot(ctypes.Structure):
                 ("pulldown_phase", c_int), ("analysed", c_int)]
 
 
+class FrameHist(ctypes.Structure):
+    _fields_ = [("frame", c_int), ("bins", ctypes.c_uint32 * 256), ("mean", c_double), ("std", c_double),
+                ("median", c_int), ("mad", c_int)]
+
+
 class Results(ctypes.Structure):
     _fields_ = [("nframes", c_int),
                 ("ncuts", c_int), ("cuts", ctypes.POINTER(c_int)),
@@ -56,7 +61,8 @@ class Results(ctypes.Structure):
                 ("label", c_int), ("field_order", c_int), ("pulldown_phase", c_int),
                 ("nkeyframes", c_int), ("keyframes", ctypes.POINTER(c_int)),
                 ("nmeasures", c_int), ("measures", ctypes.POINTER(Measure)),
-                ("motion_w", c_int), ("motion_h", c_int), ("motion", ctypes.POINTER(ctypes.c_int16))]
+                ("motion_w", c_int), ("motion_h", c_int), ("motion", ctypes.POINTER(ctypes.c_int16)),
+                ("nhist", c_int), ("hist", ctypes.POINTER(FrameHist))]
 
 
 class Profile(ctypes.Structure):

@@ -262,3 +262,25 @@ def test_cached_buffers_reused_across_clips_and_trimmed():
     assert api.N.lib.analyser_cached_bytes() > 0
     assert api.trim_cache() > 0
     assert api.N.lib.analyser_cached_bytes() == 0
+
+
+def test_frame_histograms_match_the_oracle():
+    """Per-frame histogram measure (want_histogram): bins, mean, std, median and
+    MAD of every frame equal the oracle's exactly; off by default."""
+    api = _api()
+    spec = synth.config_small()
+    frames = synth.Clip(spec).frames()
+    with api.Analyser(spec.width, spec.height, spec.fps, want_histogram=1, window_frames=24) as a:
+        a.push(frames)
+        a.finish()
+        got = a.results()
+    assert len(got["histograms"]) == len(frames)
+    for t, h in enumerate(got["histograms"]):
+        ref = OM.frame_histogram(frames[t])
+        assert h["frame"] == t
+        assert np.array_equal(h["bins"], ref["bins"]), t
+        assert (h["mean"], h["std"], h["median"], h["mad"]) == (ref["mean"], ref["std"], ref["median"], ref["mad"]), t
+    with api.Analyser(spec.width, spec.height, spec.fps) as a:
+        a.push(frames[:8])
+        a.finish()
+        assert "histograms" not in a.results()

@@ -299,3 +299,26 @@ def test_same_parity_field_pair_of_a_repeated_field_is_static():
     m = M.measure(M.LOWER_LOWER, prev, cur)
     assert m["samm"] == 0 and m["ncc"] == 1.0 and m["act"] == 0.0
     assert M.measure(M.UPPER_UPPER, prev, cur)["act"] > 0.0
+
+
+# ---- unary histogram measure --------------------------------------------------
+
+@pytest.mark.parametrize("shape,seed", [((37, 53), 1), ((64, 64), 2), ((9, 10), 3)])
+def test_frame_histogram_against_sorting_and_numpy(shape, seed):
+    rng = np.random.default_rng(seed)
+    f = rng.integers(0, 256, shape, dtype=np.uint8)
+    f[: shape[0] // 3] //= 7          # skewed content, a crowded low end
+    h = M.frame_histogram(f)
+    vals = np.sort(f.ravel().astype(np.int64))
+    k = (vals.size - 1) // 2
+    assert np.array_equal(h["bins"], np.histogram(f, bins=256, range=(0, 256))[0])
+    assert h["median"] == vals[k]
+    assert h["mad"] == np.sort(np.abs(vals - vals[k]))[k]
+    assert h["mean"] == pytest.approx(f.mean(), abs=1e-12)
+    assert h["std"] == pytest.approx(f.std(), abs=1e-12)
+
+
+def test_frame_histogram_constant_frame():
+    h = M.frame_histogram(np.full((16, 24), 77, np.uint8))
+    assert h["bins"][77] == 16 * 24 and h["bins"].sum() == 16 * 24
+    assert (h["mean"], h["std"], h["median"], h["mad"]) == (77.0, 0.0, 77, 0)
