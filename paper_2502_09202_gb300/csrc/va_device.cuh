@@ -93,10 +93,16 @@ struct RefineWin<8> {
 // then add the motion-compensated sums of their pixels (I column in registers,
 // warped J from the window) to part[] =
 // {sum I, sum J, sum I^2, sum J^2, sum IJ, sum |I-J|}.
-template <int S, int RR, int NT, int NB, int TBX, bool SUMS>
+//
+// PHASE 0 does the whole level, the parent vector of a block read from
+// s_vx/s_vy.  PHASE 1 only issues the window copies and PHASE 2 only computes
+// (the caller commits and waits in between), both with the parent passed in
+// (pvx, pvy): a kernel can then issue the first level's copies together with
+// its other loads and wait once.
+template <int S, int RR, int NT, int NB, int TBX, bool SUMS, int PHASE = 0>
 __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i, int bx0, int by0, int nbx, int nby,
                                              int lam, int* s_vx, int* s_vy, uint32_t* s_win, uint32_t (&part)[6],
-                                             int tid) {
+                                             int tid, int pvx = 0, int pvy = 0) {
   static_assert(RR == 2, "candidate ranks and window shapes assume radius 2");
   using Wn = RefineWin<S>;
   constexpr int NQ = S / 4, H = Wn::H, RT = S / H;   // column lanes, row slices, rows per slice
@@ -108,7 +114,7 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
   const int q = t % NQ, h = t / NQ;
   const int bxl = bl % TBX, byl = bl / TBX;
   const bool valid = bx0 + bxl < nbx && by0 + byl < nby;
-  const int cx = 2 * s_vx[bl], cy = 2 * s_vy[bl];
+  const int cx = 2 * (PHASE == 0 ? s_vx[bl] : pvx), cy = 2 * (PHASE == 0 ? s_vy[bl] : pvy);
   const int xw = (bx0 + bxl) * S + cx - RR;   // image position of candidate (-RR, -RR)
   const int yw = (by0 + byl) * S + cy - RR;
   const int xa = xw & ~3, s8 = 8 * (xw & 3);
@@ -120,7 +126,7 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
   // a warp instruction reads 16 contiguous bytes per block and writes 32
   // distinct banks.  A window leaving the image horizontally is read
   // clamp-to-edge, each lane its own rows.
-  if (valid) {
+  if (PHASE != 2 && valid) {
     const bool inside = xa >= 0 && xa + 4 * Wn::RW <= Jl.w;
     if (inside) {
       const uint8_t* src = Jl.p + xa + 4 * t;
@@ -140,104 +146,108 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
       }
     }
   }
-  cp_async_commit();
-  cp_async_wait_all();
-  __syncwarp();
+  if constexpr (PHASE != 1) {   // the rest computes (PHASE 1 only copies)
+    if constexpr (PHASE == 0) {
+      cp_async_commit();
+      cp_async_wait_all();
+      __syncwarp();
+    }
 
-  // ---- candidates -------------------------------------------------------------
-  uint32_t acc[5][5];   // [dx][dy]
+    // ---- candidates -------------------------------------------------------------
+    uint32_t acc[5][5];   // [dx][dy]
 #pragma unroll
-  for (int a = 0; a < 5; a++)
+    for (int a = 0; a < 5; a++)
 #pragma unroll
-    for (int d = 0; d < 5; d++) acc[a][d] = 0;
-  if (valid) {
-    uint32_t icol[RT];
-    const uint32_t* ip = s_i + (byl * S + h * RT) * IW + bxl * NQ + q;
+      for (int d = 0; d < 5; d++) acc[a][d] = 0;
+    if (valid) {
+      uint32_t icol[RT];
+      const uint32_t* ip = s_i + (byl * S + h * RT) * IW + bxl * NQ + q;
 #pragma unroll
-    for (int i = 0; i < RT; i++) icol[i] = ip[i * IW];
-    const uint32_t* wp = win + (h * RT) * Wn::RW + q;
+      for (int i = 0; i < RT; i++) icol[i] = ip[i * IW];
+      const uint32_t* wp = win + (h * RT) * Wn::RW + q;
 #pragma unroll
-    for (int w = 0; w < RT + 2 * RR; w++) {
-      const uint32_t w0 = wp[w * Wn::RW], w1 = wp[w * Wn::RW + 1], w2 = wp[w * Wn::RW + 2];
-      const uint32_t u0 = __funnelshift_r(w0, w1, s8), u1 = __funnelshift_r(w1, w2, s8);
-      const uint32_t jw[5] = {u0, __funnelshift_r(u0, u1, 8), __funnelshift_r(u0, u1, 16),
-                              __funnelshift_r(u0, u1, 24), u1};
+      for (int w = 0; w < RT + 2 * RR; w++) {
+        const uint32_t w0 = wp[w * Wn::RW], w1 = wp[w * Wn::RW + 1], w2 = wp[w * Wn::RW + 2];
+        const uint32_t u0 = __funnelshift_r(w0, w1, s8), u1 = __funnelshift_r(w1, w2, s8);
+        const uint32_t jw[5] = {u0, __funnelshift_r(u0, u1, 8), __funnelshift_r(u0, u1, 16),
+                                __funnelshift_r(u0, u1, 24), u1};
 #pragma unroll
-      for (int d = 0; d < 5; d++) {
-        const int i = w - d;
-        if (i >= 0 && i < RT) {
+        for (int d = 0; d < 5; d++) {
+          const int i = w - d;
+          if (i >= 0 && i < RT) {
 #pragma unroll
-          for (int a = 0; a < 5; a++) acc[a][d] = sad4(icol[i], jw[a], acc[a][d]);
+            for (int a = 0; a < 5; a++) acc[a][d] = sad4(icol[i], jw[a], acc[a][d]);
+          }
         }
       }
     }
-  }
-  // sum the four lanes' partials: every candidate's SAD over the block is below
-  // 2^16 (at most 256 pixels * 255), so two candidates share a 32-bit shuffle
-  // and their halves never carry into each other
-  uint32_t pk[13];
+    // sum the four lanes' partials: every candidate's SAD over the block is below
+    // 2^16 (at most 256 pixels * 255), so two candidates share a 32-bit shuffle
+    // and their halves never carry into each other
+    uint32_t pk[13];
 #pragma unroll
-  for (int j = 0; j < 13; j++) {
-    const int c0 = 2 * j, c1 = 2 * j + 1;
-    pk[j] = acc[c0 % 5][c0 / 5] | (c1 < 25 ? acc[c1 % 5][c1 / 5] << 16 : 0u);
-  }
-#pragma unroll
-  for (int off = 1; off <= 2; off <<= 1) {
-#pragma unroll
-    for (int j = 0; j < 13; j++) pk[j] += __shfl_xor_sync(0xFFFFFFFFu, pk[j], off);
-  }
-  uint32_t best = 0xFFFFFFFFu;
-  if (valid) {
-    // key = acc*256 + |v|_1*(256*lambda + 25) + 5*dy_i + dx_i - 25*min|v|_1,
-    // split into a dx part and a dy part (exact in 32 bits: key < 2^25)
-    const int n1min = max(abs(cx) - RR, 0) + max(abs(cy) - RR, 0);
-    const uint32_t k1 = (uint32_t)lam * 256u + 25u;
-    uint32_t kx[5], ky[5];
-#pragma unroll
-    for (int a = 0; a < 5; a++) kx[a] = (uint32_t)abs(cx + a - RR) * k1 + (uint32_t)a - 25u * (uint32_t)n1min;
-#pragma unroll
-    for (int d = 0; d < 5; d++) ky[d] = (uint32_t)abs(cy + d - RR) * k1 + 5u * (uint32_t)d;
-    uint32_t key[25];
-#pragma unroll
-    for (int d = 0; d < 5; d++)
-#pragma unroll
-      for (int a = 0; a < 5; a++) {
-        const int c = d * 5 + a;
-        const uint32_t sad = (c & 1) ? pk[c >> 1] >> 16 : pk[c >> 1] & 0xFFFFu;
-        key[c] = sad * 256u + kx[a] + ky[d];
-      }
-#pragma unroll
-    for (int c = 0; c < 24; c += 2) best = __vimin3_u32(best, key[c], key[c + 1]);
-    best = min(best, key[24]);
-  }
-  const int r = (int)(best & 255u) % 25;
-  if (valid && t == 0) {
-    s_vx[bl] = cx + r % 5 - RR;
-    s_vy[bl] = cy + r / 5 - RR;
-  }
-  if constexpr (SUMS) {
-    if (valid) {
-      // pixel (4q + c, i) of the block meets window byte (xw & 3) + 4q + c + dx_i of row i + dy_i
-      const int o = (xw & 3) + r % 5, dyi = r / 5, sh = 8 * (o & 3);
-      const uint32_t* ip = s_i + (byl * S + h * RT) * IW + bxl * NQ + q;
-      const uint32_t* jp = win + (h * RT + dyi) * Wn::RW + q + (o >> 2);
-      uint32_t si = 0, sj = 0, sii = 0, sjj = 0, sij = 0, sab = 0;
-#pragma unroll
-      for (int i = 0; i < RT; i++) {
-        const uint32_t iv = ip[i * IW];
-        const uint32_t w0 = jp[i * Wn::RW], w1 = sh ? jp[i * Wn::RW + 1] : 0u;
-        const uint32_t jv = __funnelshift_r(w0, w1, sh);
-        si = __dp4a(iv, 0x01010101u, si);
-        sj = __dp4a(jv, 0x01010101u, sj);
-        sii = __dp4a(iv, iv, sii);
-        sjj = __dp4a(jv, jv, sjj);
-        sij = __dp4a(iv, jv, sij);
-        sab = sad4(iv, jv, sab);
-      }
-      part[0] += si; part[1] += sj; part[2] += sii; part[3] += sjj; part[4] += sij; part[5] += sab;
+    for (int j = 0; j < 13; j++) {
+      const int c0 = 2 * j, c1 = 2 * j + 1;
+      pk[j] = acc[c0 % 5][c0 / 5] | (c1 < 25 ? acc[c1 % 5][c1 / 5] << 16 : 0u);
     }
+#pragma unroll
+    for (int off = 1; off <= 2; off <<= 1) {
+#pragma unroll
+      for (int j = 0; j < 13; j++) pk[j] += __shfl_xor_sync(0xFFFFFFFFu, pk[j], off);
+    }
+    uint32_t best = 0xFFFFFFFFu;
+    if (valid) {
+      // key = acc*256 + |v|_1*(256*lambda + 25) + 5*dy_i + dx_i - 25*min|v|_1,
+      // split into a dx part and a dy part (exact in 32 bits: key < 2^25)
+      const int n1min = max(abs(cx) - RR, 0) + max(abs(cy) - RR, 0);
+      const uint32_t k1 = (uint32_t)lam * 256u + 25u;
+      uint32_t kx[5], ky[5];
+#pragma unroll
+      for (int a = 0; a < 5; a++) kx[a] = (uint32_t)abs(cx + a - RR) * k1 + (uint32_t)a - 25u * (uint32_t)n1min;
+#pragma unroll
+      for (int d = 0; d < 5; d++) ky[d] = (uint32_t)abs(cy + d - RR) * k1 + 5u * (uint32_t)d;
+      uint32_t key[25];
+#pragma unroll
+      for (int d = 0; d < 5; d++)
+#pragma unroll
+        for (int a = 0; a < 5; a++) {
+          const int c = d * 5 + a;
+          const uint32_t sad = (c & 1) ? pk[c >> 1] >> 16 : pk[c >> 1] & 0xFFFFu;
+          key[c] = sad * 256u + kx[a] + ky[d];
+        }
+#pragma unroll
+      for (int c = 0; c < 24; c += 2) best = __vimin3_u32(best, key[c], key[c + 1]);
+      best = min(best, key[24]);
+    }
+    const int r = (int)(best & 255u) % 25;
+    if (valid && t == 0) {
+      s_vx[bl] = cx + r % 5 - RR;
+      s_vy[bl] = cy + r / 5 - RR;
+    }
+    if constexpr (SUMS) {
+      if (valid) {
+        // pixel (4q + c, i) of the block meets window byte (xw & 3) + 4q + c + dx_i of row i + dy_i
+        const int o = (xw & 3) + r % 5, dyi = r / 5, sh = 8 * (o & 3);
+        const uint32_t* ip = s_i + (byl * S + h * RT) * IW + bxl * NQ + q;
+        const uint32_t* jp = win + (h * RT + dyi) * Wn::RW + q + (o >> 2);
+        uint32_t si = 0, sj = 0, sii = 0, sjj = 0, sij = 0, sab = 0;
+#pragma unroll
+        for (int i = 0; i < RT; i++) {
+          const uint32_t iv = ip[i * IW];
+          const uint32_t w0 = jp[i * Wn::RW], w1 = sh ? jp[i * Wn::RW + 1] : 0u;
+          const uint32_t jv = __funnelshift_r(w0, w1, sh);
+          si = __dp4a(iv, 0x01010101u, si);
+          sj = __dp4a(jv, 0x01010101u, sj);
+          sii = __dp4a(iv, iv, sii);
+          sjj = __dp4a(jv, jv, sjj);
+          sij = __dp4a(iv, jv, sij);
+          sab = sad4(iv, jv, sab);
+        }
+        part[0] += si; part[1] += sj; part[2] += sii; part[3] += sjj; part[4] += sij; part[5] += sab;
+      }
+    }
+    __syncwarp();   // the next level's lanes read s_vx/s_vy and rewrite the window
   }
-  __syncwarp();   // the next level's lanes read s_vx/s_vy and rewrite the window
 }
 
 // Multiplier of the coarse candidate keys: key = cost * kCoarseKeyM + tb with

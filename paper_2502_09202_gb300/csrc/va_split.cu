@@ -131,19 +131,22 @@ __global__ void __launch_bounds__(RefineShape<TBX, TBY>::NT, RefineShape<TBX, TB
     if (bx0 + k < nbx && by0 + r / 8 < nby)
       cp_async8(&s_i1[c * 2], jb.I[1].p + (size_t)(by0 * 8 + r) * jb.I[1].pitch + (bx0 + k) * 8);
   }
-  cp_async_commit();
-  for (int i = tid; i < NB; i += NT) {
-    const int bx = bx0 + i % TBX, by = by0 + i / TBX;
-    short2 v = make_short2(0, 0);
-    if (bx < nbx && by < nby) v = jb.cvec[(size_t)by * nbx + bx];
-    s_vx[i] = v.x;
-    s_vy[i] = v.y;
-  }
-  cp_async_wait_all();
-  __syncthreads();
+  // each lane reads its block's coarse vector and issues its level-1 window
+  // copies now, so that the tile's loads all land behind one wait
   const int lam = b.cfg.lambda;
   uint32_t part[6] = {0, 0, 0, 0, 0, 0};
-  refine_level<8, 2, NT, NB, TBX, false>(jb.J[1], s_i1, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part, tid);
+  short2 pv = make_short2(0, 0);
+  {
+    const int bl = tid >> 2, bx = bx0 + bl % TBX, by = by0 + bl / TBX;
+    if (bl < NB && bx < nbx && by < nby) pv = jb.cvec[(size_t)by * nbx + bx];
+  }
+  refine_level<8, 2, NT, NB, TBX, false, 1>(jb.J[1], s_i1, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part, tid,
+                                            pv.x, pv.y);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  refine_level<8, 2, NT, NB, TBX, false, 2>(jb.J[1], s_i1, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part, tid,
+                                            pv.x, pv.y);
   refine_level<16, 2, NT, NB, TBX, true>(jb.J[0], s_i0, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part, tid);
   __syncthreads();   // every block's vector is read below
   sums_phase<TBX, TBY, NT>(b, jb, bx0, by0, 16, true, part, s_vx, s_vy, s_red, tid);

@@ -284,3 +284,22 @@ def test_frame_histograms_match_the_oracle():
         a.push(frames[:8])
         a.finish()
         assert "histograms" not in a.results()
+
+
+def test_largest_accepted_frame_size():
+    """4096x2880 (11.8 M pixels, the largest the library accepts) with a ragged
+    block grid in neither dimension; one frame pair and one field pair, value by
+    value against the oracle, and one pixel more is refused."""
+    api = _api()
+    w, h = 4096, 2880
+    spec = synth.ClipSpec(w, h, 3, 25.0, synth.TFF, 21, 3.0,
+                          synth.SceneStyle(n_objects=(6, 8), obj_speed=14, cell=8, bg_kind="textured"))
+    frames = synth.Clip(spec).frames()
+    kinds, ia, ib = [0, 1], [0, 1], [1, 2]
+    rec, mot = api.measure_pairs(_dev(frames), kinds, ia, ib, want_motion=True)
+    for k in range(len(kinds)):
+        ref, vec = _oracle_pair(kinds[k], frames[ia[k]], frames[ib[k]])
+        assert list(rec[k]) == [ref[f] for f in REC7]
+        assert np.array_equal(mot[k], vec)
+    with pytest.raises(api.AnalyserError):
+        api.Analyser(w + 2, h, 25.0)
