@@ -456,7 +456,7 @@ def run_gpu(args):
 
     # --- end to end through host buffers --------------------------------------------------
     link_gbs = _h2d_gbs(pinned, local)
-    for _ in range(max(1, args.warmup // 2)):
+    for _ in range(args.warmup):   # the first host pushes of a process run slower (copy paths warming up)
         one_step_host()
     barrier()
     torch.cuda.synchronize()
