@@ -298,6 +298,47 @@ def _warm_tiles(api, sizes):
         a.close()
 
 
+def run_configs(args):
+    """Frames/s of the analyser on each single-clip workload (small progressive,
+    1080p interlaced, 1080p 3:2 pulldown), frames resident in HBM, with the
+    decisions beside the generator's planted truth."""
+    import torch
+    from paper_2502_09202_gb300 import api, synth
+    torch.cuda.set_device(0)
+    out = []
+    for name, spec in (("small", synth.config_small()), ("interlaced", synth.config_interlaced()),
+                       ("pulldown", synth.config_pulldown())):
+        clip = synth.Clip(spec)
+        host = _make_frames(spec, 0)
+        dev = torch.from_numpy(host).cuda()
+        T, H, W = host.shape
+
+        def step():
+            a = api.Analyser(W, H, spec.fps, window_frames=args.window)
+            a.push_device(dev)
+            a.finish()
+            r = a.results()
+            a.close()
+            return r
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            r = step()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        truth = clip.truth()
+        out.append({"config": name, "frames": T, "size": f"{W}x{H}", "value": T / dt, "unit": "frames/s",
+                    "x_realtime": T / dt / spec.fps, "ms_per_clip": 1e3 * dt,
+                    "cuts": r["cuts"], "truth_cuts": truth["cuts"], "dissolves": r["dissolves"],
+                    "truth_dissolves": truth["dissolves"], "label": r["label"], "truth_structure": truth["structure"],
+                    "pulldown_phase": r["pulldown_phase"], "truth_phase": truth["pulldown_phase"]})
+    print(json.dumps({"mode": "configs", "results": out}))
+    return 0
+
+
 def run_batched(args):
     """Batched workload (uneven clips, every structure, several resolutions): the
     plain path analyses clip after clip; the batched path runs them all through
@@ -530,7 +571,7 @@ def main():
     ap.add_argument("--ref-frames", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--window", type=int, default=512, help="frames resident per clip (1.7 GB at 1080p)")
-    ap.add_argument("--mode", default="clip", choices=["clip", "kernel", "batched", "served"])
+    ap.add_argument("--mode", default="clip", choices=["clip", "kernel", "batched", "served", "configs"])
     ap.add_argument("--clips", type=int, default=64)
     ap.add_argument("--requests", type=int, default=512)
     ap.add_argument("--rate", type=float, default=40.0)
@@ -546,6 +587,8 @@ def main():
         return run_batched(args)
     if args.mode == "served":
         return run_served(args)
+    if args.mode == "configs":
+        return run_configs(args)
     return run_gpu(args)
 
 
