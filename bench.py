@@ -30,7 +30,7 @@ WORKLOAD = "interlaced-tff-1920x1080x1500@25fps"
 # dram__bytes_read.sum + dram__bytes_write.sum of coarse_kernel + refine_kernel for 16 frame
 # pairs of this workload (one ncu --set full capture of `--mode kernel --pairs 64`), per pair;
 # to be re-taken whenever either kernel changes
-PAIR_KERNEL_DRAM_BYTES_PER_PAIR = (2.235136e6 + 44.858368e6 + 0.159744e6) / 16
+PAIR_KERNEL_DRAM_BYTES_PER_PAIR = (2.235648e6 + 44.858880e6 + 0.161024e6) / 16
 METRIC = "frames/s at 1080p luma (full analysis: measures + decisions)"
 
 
@@ -351,26 +351,39 @@ def run_batched(args):
     clips = _gen_clips(specs)
     frames = sum(len(c) for c in clips)
     _warm_tiles(api, [(s.width, s.height) for s in specs])
+
+    def plain_pass():
+        out, launches = [], 0
+        for s, f in zip(specs, clips):
+            with api.Analyser(s.width, s.height, s.fps) as a:
+                a.push(f)
+                a.finish()
+                out.append(a.results())
+                launches += a.stats()["launches"]
+        return out, launches
+
+    def batched_pass():
+        srv = api.Server(budget_bytes=int(args.budget_gb * (1 << 30)))
+        tickets = [srv.submit(f, s.fps) for s, f in zip(specs, clips)]
+        srv.drain()
+        out = [srv.poll(t) for t in tickets]
+        prof = srv.profile()
+        srv.close()
+        return out, prof
+
+    # one untimed pass of each path fills the process's memory cache for every
+    # size the workload needs, so that neither timed pass pays for first allocations
+    plain_pass()
+    batched_pass()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    plain = []
-    launches_plain = 0
-    for s, f in zip(specs, clips):
-        with api.Analyser(s.width, s.height, s.fps) as a:
-            a.push(f)
-            a.finish()
-            plain.append(a.results())
-            launches_plain += a.stats()["launches"]
+    plain, launches_plain = plain_pass()
     t_plain = time.perf_counter() - t0
-    srv = api.Server(budget_bytes=int(args.budget_gb * (1 << 30)))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    tickets = [srv.submit(f, s.fps) for s, f in zip(specs, clips)]
-    srv.drain()
+    batched, prof = batched_pass()
     t_batched = time.perf_counter() - t0
-    prof = srv.profile()
-    same = all(_same_decisions(srv.poll(t), p) for t, p in zip(tickets, plain))
-    srv.close()
+    same = all(_same_decisions(b, p) for b, p in zip(batched, plain))
     print(json.dumps({
         "mode": "batched", "metric": "frames/s (host frames in, results out)", "unit": "frames/s",
         "clips": len(specs), "frames": frames, "pixels": sum(s.pixels * s.nframes for s in specs),
@@ -395,6 +408,13 @@ def run_served(args):
     clips = _gen_clips([s for _, s in reqs])
     frames = sum(len(c) for c in clips)
     _warm_tiles(api, [(s.width, s.height) for _, s in reqs])
+    # a running service is warm: one untimed pass of the same requests, all at
+    # once, fills the memory cache for every clip size before the arrivals start
+    warm = api.Server(budget_bytes=int(args.budget_gb * (1 << 30)))
+    for i, (_, s) in enumerate(reqs):
+        warm.submit(clips[i], s.fps)
+    warm.drain()
+    warm.close()
     srv = api.Server(budget_bytes=int(args.budget_gb * (1 << 30)))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -429,6 +449,9 @@ def run_served(args):
         "value": frames / t_total, "seconds": t_total, "last_arrival_s": reqs[-1][0],
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                       "max": float(lat.max())},
+        "slowest": [{"request": int(i), "arrival_s": round(reqs[i][0], 4), "frames": len(clips[i]),
+                     "size": f"{reqs[i][1].width}x{reqs[i][1].height}", "latency_s": round(float(lat[i]), 5)}
+                    for i in np.argsort(-lat)[:5]],
         "waves": prof["waves"], "launches": prof["launches"], "pairs": prof["pairs"],
         "identical_to_alone": same, "checked": len(check)}))
     return 0
