@@ -36,21 +36,21 @@ struct RefineShape {
   static constexpr int MINB = VA_REFINE_MINB * 128 / NT;  // resident CTAs per SM the register budget allows
 };
 
-// The job holding `item` (the last job whose first item is <= item): each
-// warp compares 32 jobs per step with one ballot.  Called by whole warps.
-__device__ __forceinline__ int find_job(const PairBatch& b, int item) {
-  const int lane = threadIdx.x & 31;
-  for (int base = 0;; base += 32) {
-    const int j = base + lane;
-    const unsigned m = __ballot_sync(0xFFFFFFFFu, j < b.njobs && b.jobs[j].item_begin <= item);
-    if (m != 0xFFFFFFFFu || base + 32 >= b.njobs) return base + __popc(m) - 1;
-  }
-}
-
+// Copies the job holding `item` to shared memory: thread t checks jobs t,
+// t + NT, ... at once (item_begin[j] <= item < item_begin[j + 1]; exactly one
+// job matches, also with empty jobs), so the lookup costs one round trip to L2 whatever the
+// number of jobs.  Called by the whole CTA; ends with a barrier.
 template <int NT>
-__device__ __forceinline__ void copy_job(const PairBatch& b, int item, PairJob* dst, int tid) {
-  const int* src = reinterpret_cast<const int*>(b.jobs + find_job(b, item));
+__device__ __forceinline__ void copy_job(const PairBatch& b, int item, PairJob* dst, int* s_jidx, int tid) {
+  for (int j = tid; j < b.njobs; j += NT) {
+    const int beg = b.jobs[j].item_begin;
+    const int next = j + 1 < b.njobs ? b.jobs[j + 1].item_begin : 0x7FFFFFFF;
+    if ((j == 0 || beg <= item) && item < next) *s_jidx = j;   // item_begin is nondecreasing: one match
+  }
+  __syncthreads();
+  const int* src = reinterpret_cast<const int*>(b.jobs + *s_jidx);
   for (int i = tid; i < (int)(sizeof(PairJob) / 4); i += NT) reinterpret_cast<int*>(dst)[i] = src[i];
+  __syncthreads();
 }
 
 template <int R, int TBX, int TBY>
@@ -62,9 +62,9 @@ __global__ void __launch_bounds__(CoarseShape<R, TBX, TBY>::NT, CoarseShape<R, T
   __shared__ uint32_t s_best32[NB];
   __shared__ int s_vx[NB], s_vy[NB];
   __shared__ PairJob s_job;
+  __shared__ int s_jidx;
   const int tid = threadIdx.x, item = blockIdx.x;
-  copy_job<NT>(b, item, &s_job, tid);
-  __syncthreads();
+  copy_job<NT>(b, item, &s_job, &s_jidx, tid);
   const PairJob& jb = s_job;
   const int local = item - jb.item_begin;
   const int bx0 = (local % jb.tiles_x) * TBX, by0 = (local / jb.tiles_x) * TBY;
@@ -114,9 +114,9 @@ __global__ void __launch_bounds__(RefineShape<TBX, TBY>::NT, RefineShape<TBX, TB
   __shared__ int s_vx[NB], s_vy[NB];
   __shared__ unsigned long long s_red[NT / 32][kRecWords];
   __shared__ PairJob s_job;
+  __shared__ int s_jidx;
   const int tid = threadIdx.x, item = blockIdx.x;
-  copy_job<NT>(b, item, &s_job, tid);
-  __syncthreads();
+  copy_job<NT>(b, item, &s_job, &s_jidx, tid);
   const PairJob& jb = s_job;
   const int local = item - jb.item_begin;
   const int bx0 = (local % jb.tiles_x) * TBX, by0 = (local / jb.tiles_x) * TBY;
