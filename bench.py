@@ -30,7 +30,7 @@ WORKLOAD = "interlaced-tff-1920x1080x1500@25fps"
 # dram__bytes_read.sum + dram__bytes_write.sum of coarse_kernel + refine_kernel for 16 frame
 # pairs of this workload (one ncu --set full capture of `--mode kernel --pairs 64`), per pair;
 # to be re-taken whenever either kernel changes
-PAIR_KERNEL_DRAM_BYTES_PER_PAIR = (2.235648e6 + 44.858880e6 + 0.161024e6) / 16
+PAIR_KERNEL_DRAM_BYTES_PER_PAIR = (2.236928e6 + 45.086720e6 + 0.170240e6) / 16
 METRIC = "frames/s at 1080p luma (full analysis: measures + decisions)"
 
 

@@ -59,9 +59,14 @@ int fail_srv(server* s, int code, const std::string& why) {
 }
 
 // Run waves until the clip's detector is done (finish) or no more progress is
-// possible without new frames.
+// possible without new frames.  Short of the end, it also returns for more
+// frames once a quarter of the window is free, even with deep checks still
+// requested: the next wave then carries those checks beside the new frames'
+// adjacent pairs (fewer, fuller waves; every measure is the same whichever
+// wave computes it).
 int drive(analyser* a, bool to_end) {
   va::Engine& e = *a->eng;
+  const int merge_slots = std::max(32, a->clip.cap / 4);
   for (;;) {
     const int rc = e.wave();
     if (rc < 0 || e.status) return fail(a, e.status ? e.status : rc, e.message);
@@ -70,7 +75,9 @@ int drive(analyser* a, bool to_end) {
       if (to_end) return fail(a, ANALYSER_ERR_STATE, "analysis stalled before the end of the clip");
       return ANALYSER_OK;
     }
-    if (!to_end && e.free_slots(&a->clip) > 0 && a->clip.pending.empty()) return ANALYSER_OK;
+    if (to_end) continue;
+    const int free = e.free_slots(&a->clip);
+    if ((free > 0 && a->clip.pending.empty()) || free >= merge_slots) return ANALYSER_OK;
   }
 }
 
