@@ -283,9 +283,12 @@ void Engine::remove_clip(Clip* c) {
     c->up_chunks.clear();
   }
   if (c->d_ring) {
-    // the window returns to the cache: nothing queued may still read or write it
+    // the window returns to the cache: nothing queued may still read or write
+    // it.  The clip's own copies have all landed (its chunk list is empty), and
+    // the copy stream's other work is other clips' frames, so only the compute
+    // streams are waited for: with many clips in flight, waiting for the copy
+    // stream would hold every retirement until all queued frames had landed.
     cudaStreamSynchronize(stream);
-    cudaStreamSynchronize(cstream);
     cudaStreamSynchronize(rstream);
     pool_free(c->d_ring);
     c->d_ring = nullptr;

@@ -216,6 +216,27 @@ def test_long_clip_streams_through_a_small_window():
             _compare_results(a.results(), ref)
 
 
+def test_long_clip_device_pushes_any_window():
+    """Device pushes of a clip several windows long, whole and in uneven chunks,
+    through windows below and above the size at which new frames join waves that
+    still carry deep checks: the decisions must not depend on how the waves were
+    composed."""
+    api = _api()
+    spec = synth.config_interlaced(nframes=260, width=256, height=144)
+    frames = synth.Clip(spec).frames()
+    ref = OA.analyse_frames(frames)
+    dev = _dev(frames)
+    for window in (24, 64, 128, 300):
+        for chunks in ((260,), (7, 100, 1, 152)):
+            with api.Analyser(spec.width, spec.height, spec.fps, window_frames=window) as a:
+                s = 0
+                for c in chunks:
+                    a.push_device(dev[s:s + c])
+                    s += c
+                a.finish()
+                _compare_results(a.results(), ref)
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_split_and_fused_kernels_match_the_oracle(mode):
     """kernel_mode 0 runs the coarse and refinement kernels on two streams,
