@@ -1,10 +1,12 @@
 """Host-side checks that need no GPU: the C ABI loads and exports what the header
 declares, argument validation, and the library's own detectors (C++) driven by
-oracle measures reproduce the oracle's decisions and FP64 values exactly."""
+oracle measures reproduce the oracle's decisions and FP64 values exactly; on
+scripted records they also reach the decisions derived by hand from the rules."""
 import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from oracle import analyser as OA
@@ -116,3 +118,101 @@ def test_offline_callback_errors_surface(native):
 
     with pytest.raises(ValueError):
         api.detect_offline(320, 180, 5, bad)
+
+
+# ---- the library's detectors on scripted records ---------------------------------
+# A record with S_i = S_j = S_ij = 0 and S_ii = S_jj = 1 has C = 0 and Vi, Vj > 0,
+# so NCC = 0 and SWR = 1, and S_amm = ACT^2 * 65536 * nb makes ACT = sqrt(AMM) the
+# scripted value.  The expected decisions are derived by hand from the rules
+# (Sec. III.B-D), as in the oracle's detector pins; the oracle run on the same
+# records must agree on everything.
+
+def _scripted_record(act, kind, a, b):
+    n, nb = (64 * 64, 16) if kind == OM.FRAME else (64 * 32, 8)
+    return [0, 0, 1, 1, 0, 0, int(round(act * act * 65536 * nb)), n, nb]
+
+
+def _both(T, act):
+    """Library and oracle decisions for a 64x64 clip of T frames whose pair
+    (kind, a, b) has ACT = act(kind, a, b)."""
+    from paper_2502_09202_gb300 import api
+
+    def get(kind, a, b):
+        return _scripted_record(act(kind, a, b), kind, a, b)
+
+    got = api.detect_offline(64, 64, T, get)
+
+    class Records(OA.OracleAnalyser):
+        def m(self, kind, a, b):
+            key = (kind, a, b)
+            if key not in self.cache:
+                self.cache[key] = OM.finalise(dict(zip(OM.REC_FIELDS, get(kind, a, b))))
+            return self.cache[key]
+
+    ref = Records(lambda t: np.zeros((64, 64), np.uint8), T).run()
+    _same(got, ref)
+    return got
+
+
+def _positions(p, field_act=1.0):
+    def act(kind, a, b):
+        return 1.0 + 9.0 * abs(p(a) - p(b)) if kind == OM.FRAME else field_act
+    return act
+
+
+def _requested(r):
+    return sorted((a, b) for (k, a, b) in r["measures"] if k == OM.FRAME and b != a + 1)
+
+
+def test_library_hard_cut_on_scripted_records(native):
+    r = _both(12, _positions(lambda f: 0.0 if f <= 6 else 1.0))
+    assert r["cuts"] == [7] and r["dissolves"] == []
+    assert r["keyframes"] == [0, 7]
+    assert _requested(r) == [(6, 4), (6, 5), (6, 8)]
+
+
+def test_library_dissolve_on_scripted_records(native):
+    p = {11: 1 / 3, 12: 2 / 3}
+    r = _both(20, _positions(lambda f: 0.0 if f <= 10 else p.get(f, 1.0)))
+    assert r["dissolves"] == [(10, 3)] and r["cuts"] == []
+    assert r["keyframes"] == [0, 9, 13]
+    assert _requested(r) == [(10, 8), (10, 9), (10, 12), (10, 13), (10, 14)]
+
+
+def test_library_ramp_start_on_scripted_records(native):
+    steps = {11: 0.5 / 9, 12: 1.3 / 9, 13: 2.4 / 9}
+    r = _both(20, _positions(lambda f: 0.0 if f <= 10 else steps.get(f, 1.0)))
+    assert r["dissolves"] == [(10, 4)] and r["cuts"] == []
+
+
+def test_library_keyframes_on_scripted_records(native):
+    assert _both(12, lambda k, a, b: 3.0)["keyframes"] == [0, 3, 6, 9]
+
+
+@pytest.mark.parametrize("v,label,fo", [
+    ((5.0, 6.0, 3.0), OA.INTERLACED, OA.FO_TFF),
+    ((5.0, 3.0, 6.0), OA.INTERLACED, OA.FO_BFF),
+    ((5.0, 3.0, 3.0), OA.PROGRESSIVE, OA.FO_NONE),
+    ((0.1, 1.0, 1.0), OA.PROGRESSIVE, OA.FO_NONE),
+])
+def test_library_structure_on_scripted_records(native, v, label, fo):
+    def act(kind, a, b):
+        if kind == OM.FRAME:
+            return 1.0                      # AMM = 1 px: not static
+        if kind == OM.UPPER_LOWER:
+            return v[0] if a == b else v[1]
+        return v[2]
+    r = _both(30, act)
+    assert (r["label"], r["field_order"]) == (label, fo)
+
+
+@pytest.mark.parametrize("phase", [0, 2, 3])
+def test_library_pulldown_phase_on_scripted_records(native, phase):
+    def act(kind, a, b):
+        if kind == OM.FRAME:
+            return 1.0
+        if kind == OM.UPPER_LOWER and a == b:
+            return 5.0 if (a - phase) % 5 in (2, 3) else 0.1
+        return 1.0
+    r = _both(30, act)
+    assert (r["label"], r["pulldown_phase"]) == (OA.PULLDOWN, phase)
