@@ -216,3 +216,18 @@ def test_library_pulldown_phase_on_scripted_records(native, phase):
         return 1.0
     r = _both(30, act)
     assert (r["label"], r["pulldown_phase"]) == (OA.PULLDOWN, phase)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the compiled library the package refuses to import: there is no
+    CPU fallback behind the API."""
+    import shutil
+    import subprocess
+    import sys
+    src = os.path.join(ROOT, "paper_2502_09202_gb300")
+    dst = tmp_path / "paper_2502_09202_gb300"
+    shutil.copytree(src, dst, ignore=shutil.ignore_patterns("*.so", "_build", "__pycache__", "csrc"))
+    for mod in ("native", "api"):
+        p = subprocess.run([sys.executable, "-c", f"import paper_2502_09202_gb300.{mod}"], cwd=tmp_path,
+                           capture_output=True, text=True, env={**os.environ, "PYTHONPATH": str(tmp_path)})
+        assert p.returncode != 0 and "ImportError" in p.stderr and "libgb300va.so is missing" in p.stderr, p.stderr
