@@ -35,7 +35,7 @@ extern "C" {
 #define ANALYSER_ERR_INVALID_ARG (-1) /* null pointer, bad size/pitch, unsupported parameters */
 #define ANALYSER_ERR_OOM (-2)         /* device or host allocation failed, or budget exceeded */
 #define ANALYSER_ERR_CUDA (-3)        /* a CUDA call failed (the message says which) */
-#define ANALYSER_ERR_TIMEOUT (-4)     /* a bounded device wait gave up */
+#define ANALYSER_ERR_TIMEOUT (-4)     /* a bounded wait gave up (params.wait_timeout_ms) */
 #define ANALYSER_ERR_STATE (-5)       /* call not allowed in this state (e.g. push after finish) */
 #define ANALYSER_PENDING 1            /* server_poll: the request is not done yet */
 
@@ -53,9 +53,10 @@ extern "C" {
 #define ANALYSER_PAIR_UPPER_LOWER 1 /* I = upper field of a, J = lower field of b */
 #define ANALYSER_PAIR_LOWER_UPPER 2 /* I = lower field of a, J = upper field of b */
 /* Same-parity field pairs: an extension for repeated-field detection in the
- * spirit of Sec. III.C (the paper measures only v0, v1, v2).  Available through
- * analyser_measure_pairs and analyser_measure_pair_noalloc; the detectors do
- * not use them. */
+ * spirit of Sec. III.C (the paper measures only v0, v1, v2).  The sampling
+ * detector reads them for its voters to find the repeated fields of 3:2
+ * pulldown; analyser_measure_pairs and analyser_measure_pair_noalloc take them
+ * too. */
 #define ANALYSER_PAIR_UPPER_UPPER 3 /* I = upper field of a, J = upper field of b */
 #define ANALYSER_PAIR_LOWER_LOWER 4 /* I = lower field of a, J = lower field of b */
 
@@ -81,17 +82,33 @@ typedef struct {
   double fast_tau;     /*                                                    (0.5) */
   double deep_rho;     /* x << y  iff  deep_rho*x + deep_tau < y             (2.0) */
   double deep_tau;     /*                                                    (0.5) */
+  double done_eps;     /* transition complete at t+K: ACT(t,t+K+1) <= (1+done_eps)*ACT(t,t+K) (0.25) */
+  double steady_gamma; /* dissolve K >= 2: a_t+K+d <= steady_gamma * max of the next
+                          steady_frames values, d = 0..steady_span-1          (1.2) */
+  int steady_frames;   /*                                                    (4) */
+  int steady_span;     /*                                                    (2) */
+  double lag_rho;      /* dissolve K >= 2: ACT(t,t+K) > lag_rho * ACT(t,t-K)  (1.5) */
+  double blend_ratio;  /* dissolve K >= 2: ACT(t,t+K-1) >= blend_ratio * ACT(t,t+K) (0.6) */
+  double pd_rho;       /* 3:2 pulldown shots: candidate and cut iff a_t > pd_rho * the same
+                          cadence step one 5-frame unit earlier              (1.4) */
+  double pd_gamma_new; /* ... and a_t+1 <= pd_gamma_new * a_t-4 (steady new shot) (2.5) */
+  double pd_gamma_old; /* ... and a_t-1 <= pd_gamma_old * a_t-6 (t is no flash)  (1.4) */
   /* sampling structure (Sec. III.C) */
-  int samp_max_frames;   /* frames analysed per shot                          (20) */
+  int samp_max_frames;   /* frames analysed per shot (N_s)                    (20) */
   double static_amm_px;  /* frames with AMM(t,t+1) below this are skipped     (0.5) */
-  double comb_ratio;     /* combed iff v0 > comb_ratio * max(v1,v2)            (0.3) */
-  double unequal_ratio;  /* interlaced needs median(v1/v2) > this or < 1/this (1.12) */
-  double pulldown_match; /* fraction of frames matching the 3:2 comb pattern  (0.8) */
+  double comb_ratio;     /* combed iff AMM(v0) > comb_ratio * min(AMM(v1), AMM(v2)) (0.65) */
+  double unequal_ratio;  /* interlaced needs median(AMM(v1)/AMM(v2)) > this or < 1/this (1.04) */
+  double rep_ratio;      /* repeated field: ACT(u_t,u_t+1) < rep_ratio * ACT(l_t,l_t+1), or
+                            the same with the fields swapped                 (0.25) */
+  int rep_probe;         /* voters that always read the same-parity pairs     (5) */
+  double pulldown_match; /* fraction of voters matching the 3:2 repeated-field pattern (0.8) */
   /* dynamic keyframes (Sec. III.D) */
   double kf_theta;       /* keyframe when the accumulated activity exceeds this (8.0) */
   /* resources */
   int device;                          /* CUDA device ordinal                 (0) */
-  int window_frames;                   /* rolling window of frames on the device (0 = auto) */
+  int window_frames;                   /* rolling window of frames on the device: 0 = auto (max(96,
+                                          2*kmax + steady_span + steady_frames + 6)), else at least
+                                          2*kmax + steady_span + steady_frames + 4 */
   unsigned long long mem_budget_bytes; /* device memory cap for one analyser (0 = none) */
   int want_motion;                     /* keep level-0 motion fields of frame pairs (t,t+1) (0) */
   int tile_x, tile_y;                  /* pair-kernel tile in blocks (8x4, 4x4, 8x2, 16x2, 4x8);
@@ -102,6 +119,9 @@ typedef struct {
                                           estimator (levels 3, radius_refine 2), fused otherwise;
                                           1: always the fused kernel (0) */
   int want_histogram;                  /* per-frame luma histogram and its statistics (0) */
+  double wait_timeout_ms;              /* host watchdog: a wave or frame copy not complete after this
+                                          many ms fails the call with ANALYSER_ERR_TIMEOUT (sticky);
+                                          0 = wait without a limit (0) */
 } analyser_params;
 
 /* One measure of one pair, in the order of (kind, a, b). */
@@ -161,6 +181,8 @@ int analyser_default_params(analyser_params* p);
  * Create an analyser for a clip of width x height luma frames at `fps` frames/s.
  * Requirements: 64 <= width, 64 <= height, height even, width*height <= 11,800,000
  * (exact 64-bit correlation sums), parameters within the ranges above.
+ * ANALYSER_ERR_OOM when the rolling window exceeds params.mem_budget_bytes
+ * (checked before any device work) or its allocation fails.
  * On success *out owns the device buffers of the rolling frame window.
  */
 int analyser_create(int width, int height, double fps, const analyser_params* p, analyser** out);
@@ -169,14 +191,15 @@ int analyser_create(int width, int height, double fps, const analyser_params* p,
  * Append `nframes` frames from HOST memory (frame k at luma + k*height*pitch_bytes,
  * rows pitch_bytes apart, pitch_bytes >= width).  The frames are copied; the
  * caller keeps ownership.  Runs GPU work as the window fills; returns when all
- * frames are copied.  Error ANALYSER_ERR_STATE after analyser_finish.
+ * frames are copied.  A push after analyser_finish fails with ANALYSER_ERR_STATE,
+ * and like every failure that code sticks to the handle.
  */
 int analyser_push_frames(analyser* a, const uint8_t* luma, long long pitch_bytes, int nframes);
 
 /*
  * Append `nframes` frames already resident in DEVICE memory (frame k at
- * luma + k*frame_stride_bytes; pitch_bytes a multiple of 16, luma 16-byte
- * aligned).  No copy is made: the buffer must stay valid and unchanged until
+ * luma + k*frame_stride_bytes; pitch_bytes a multiple of 16 and at most
+ * INT_MAX/2, luma 16-byte aligned).  No copy is made: the buffer must stay valid and unchanged until
  * analyser_finish returns.
  */
 int analyser_push_frames_device(analyser* a, const uint8_t* luma, long long pitch_bytes,
@@ -186,8 +209,9 @@ int analyser_push_frames_device(analyser* a, const uint8_t* luma, long long pitc
 int analyser_finish(analyser* a);
 
 /*
- * Results after analyser_finish.  Pointers are owned by the analyser and stay
- * valid until the next call on it or analyser_destroy.
+ * Results after analyser_finish (ANALYSER_ERR_STATE before it, without making
+ * the handle fail).  Pointers are owned by the analyser and stay valid until
+ * the next call on it or analyser_destroy.
  */
 int analyser_results(analyser* a, analyser_results_t* out);
 
@@ -220,7 +244,8 @@ void analyser_destroy(analyser* a);
  * frames + f*frame_stride_bytes) with pair kind kinds[k] (ANALYSER_PAIR_FRAME ..
  * ANALYSER_PAIR_LOWER_LOWER; field kinds need an even height).  records receives
  * 7 int64 per pair (sum i, sum j, sum i^2, sum j^2, sum i*j, sum |i-j|, S_amm)
- * in HOST memory; motion (optional, HOST) receives the level-0 field of every
+ * in HOST memory (pitch_bytes a multiple of 16 and at most INT_MAX/2, frames
+ * 16-byte aligned); motion (optional, HOST) receives the level-0 field of every
  * pair, nby*nbx (vx, vy) int16 each.  `stream` is a cudaStream_t (0 = default).
  * Takes its pyramids and queues from the library's resource cache for the
  * duration of the call.
@@ -242,10 +267,13 @@ int analyser_measure_pairs(const analyser_params* p, int width, int height, cons
  * Its scratch (pyramids, descriptors, accumulators) is a fixed 5.5 MiB device
  * array inside this library, present on every device that loads it until the
  * process exits: 3840x2160 frames fit, larger scratch needs are rejected with
- * ANALYSER_ERR_INVALID_ARG.  Only params levels = 3, block = 16.  The array is
- * shared by all calls: calls whose GPU work overlaps race on it.  The first
- * call with a given device current looks up the array's device address; make
- * it before any stream capture.  Returns after the record is in `record`.
+ * ANALYSER_ERR_INVALID_ARG, as is a pitch_bytes above INT_MAX/2.  Only params
+ * levels = 3, block = 16.  The array is shared by all calls: calls whose GPU
+ * work overlaps race on it.  The first call for a device (params.device) looks
+ * up the array's device address with that device current; make that first
+ * call before any stream capture.  Every call waits for `stream` and returns
+ * once the record is in `record`; the calling thread's current device is the
+ * same after the call as before it.
  */
 int analyser_measure_pair_noalloc(const analyser_params* p, int width, int height, int kind,
                                   const uint8_t* frame_a, const uint8_t* frame_b, long long pitch_bytes,

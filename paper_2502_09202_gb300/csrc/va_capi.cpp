@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -101,10 +102,21 @@ int analyser_default_params(analyser_params* p) {
   p->fast_tau = 0.5;
   p->deep_rho = 2.0;
   p->deep_tau = 0.5;
+  p->done_eps = 0.25;
+  p->steady_gamma = 1.2;
+  p->steady_frames = 4;
+  p->steady_span = 2;
+  p->lag_rho = 1.5;
+  p->blend_ratio = 0.6;
+  p->pd_rho = 1.4;
+  p->pd_gamma_new = 2.5;
+  p->pd_gamma_old = 1.4;
   p->samp_max_frames = 20;
   p->static_amm_px = 0.5;
-  p->comb_ratio = 0.3;
-  p->unequal_ratio = 1.12;
+  p->comb_ratio = 0.65;
+  p->unequal_ratio = 1.04;
+  p->rep_ratio = 0.25;
+  p->rep_probe = 5;
   p->pulldown_match = 0.8;
   p->kf_theta = 8.0;
   p->device = 0;
@@ -117,6 +129,7 @@ int analyser_default_params(analyser_params* p) {
   p->step_frames = 32;
   p->kernel_mode = 0;
   p->want_histogram = 0;
+  p->wait_timeout_ms = 0.0;
   return ANALYSER_OK;
 }
 
@@ -129,6 +142,14 @@ int analyser_create(int width, int height, double fps, const analyser_params* p,
   if (!rc) rc = va::validate_size(width, height, *p, why);
   if (rc) return rc;
   if (!(fps > 0)) return ANALYSER_ERR_INVALID_ARG;
+  {
+    // the window's bytes are known from the sizes alone: refuse an over-budget
+    // clip before touching the device
+    va::Geometry g;
+    g.init(width, height, p->levels);
+    const int cap = p->window_frames > 0 ? p->window_frames : std::max(96, va::min_window(*p) + 2);
+    if (p->mem_budget_bytes && va::Engine::ring_bytes(g, cap) > p->mem_budget_bytes) return ANALYSER_ERR_OOM;
+  }
   analyser* a = new (std::nothrow) analyser();
   if (!a) return ANALYSER_ERR_OOM;
   a->eng.reset(new (std::nothrow) va::Engine(*p));
@@ -153,7 +174,7 @@ int analyser_push_frames(analyser* a, const uint8_t* luma, long long pitch_bytes
   if (!a) return ANALYSER_ERR_INVALID_ARG;
   if (a->status) return a->status;
   if (a->offline) return ANALYSER_ERR_STATE;
-  if (a->clip.finished) return ANALYSER_ERR_STATE;
+  if (a->clip.finished) return fail(a, ANALYSER_ERR_STATE, "push after analyser_finish");
   if (nframes < 0 || (nframes > 0 && !luma) || pitch_bytes < a->clip.geo.W) return ANALYSER_ERR_INVALID_ARG;
   if (a->clip.external_l0) return fail(a, ANALYSER_ERR_STATE, "host and device pushes cannot be mixed");
   va::Engine& e = *a->eng;
@@ -203,9 +224,12 @@ int analyser_push_frames_device(analyser* a, const uint8_t* luma, long long pitc
                                 int nframes) {
   if (!a) return ANALYSER_ERR_INVALID_ARG;
   if (a->status) return a->status;
-  if (a->offline || a->clip.finished) return ANALYSER_ERR_STATE;
+  if (a->offline) return ANALYSER_ERR_STATE;
+  if (a->clip.finished) return fail(a, ANALYSER_ERR_STATE, "push after analyser_finish");
+  // field views double the pitch, and the kernels' plane descriptors hold it in an int
   if (nframes < 0 || (nframes > 0 && !luma) || pitch_bytes < a->clip.geo.W || pitch_bytes % 16 ||
-      frame_stride_bytes % 16 || ((uintptr_t)luma % 16) || frame_stride_bytes < pitch_bytes * a->clip.geo.H)
+      pitch_bytes > INT_MAX / 2 || frame_stride_bytes % 16 || ((uintptr_t)luma % 16) ||
+      frame_stride_bytes < pitch_bytes * a->clip.geo.H)
     return ANALYSER_ERR_INVALID_ARG;
   if (a->clip.pushed > 0 && !a->clip.external_l0)
     return fail(a, ANALYSER_ERR_STATE, "host and device pushes cannot be mixed");
@@ -235,7 +259,9 @@ int analyser_finish(analyser* a) {
   a->clip.finished = true;
   const int rc = drive(a, true);
   if (rc) return rc;
-  if (cudaStreamSynchronize(a->eng->stream) != cudaSuccess) return fail(a, ANALYSER_ERR_CUDA, "cudaStreamSynchronize");
+  const cudaError_t e = a->eng->wait_stream(a->eng->stream);
+  if (e == cudaErrorTimeout) return fail(a, ANALYSER_ERR_TIMEOUT, "analyser_finish: GPU work not complete in wait_timeout_ms");
+  if (e != cudaSuccess) return fail(a, ANALYSER_ERR_CUDA, "cudaStreamSynchronize");
   return ANALYSER_OK;
 }
 
@@ -383,7 +409,7 @@ int server_submit(server* s, int width, int height, double fps, const uint8_t* f
   // window size is fixed at admission; estimate its bytes now for the budget
   va::Geometry g;
   g.init(width, height, s->p.levels);
-  const int cap = s->p.window_frames > 0 ? s->p.window_frames : std::max(96, 2 * s->p.kmax + 8);
+  const int cap = s->p.window_frames > 0 ? s->p.window_frames : std::max(96, va::min_window(s->p) + 2);
   r.bytes = va::Engine::ring_bytes(g, cap);
   if (s->budget && r.bytes > s->budget) {
     s->reqs.erase(t);

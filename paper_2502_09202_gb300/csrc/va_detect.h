@@ -49,7 +49,9 @@ struct ShotOut {
 
 class Detector {
  public:
-  enum Status { kProgress = 0, kNeedPairs = 1, kNeedFrames = 2, kDone = 3 };
+  // kNeedVotes is internal: the shot detector waits for the sampling detector's
+  // verdict on the current shot (run() reports it as kNeedPairs)
+  enum Status { kProgress = 0, kNeedPairs = 1, kNeedFrames = 2, kDone = 3, kNeedVotes = 4 };
 
   Detector() = default;
   void reset(const analyser_params& p, int64_t nb);
@@ -71,19 +73,25 @@ class Detector {
   int clip_label = ANALYSER_UNKNOWN, clip_fo = ANALYSER_FO_NONE, clip_phase = -1;
 
  private:
-  struct Sample { int t; double v0, v1, v2; };
+  enum { kRepNone = 0, kRepUpper = 1, kRepLower = 2 };
+  struct Vote { int t; double a0, a1, a2; };   // AMM of v0, v1, v2
   struct Shot {
     int first = 0, last = -1;
     std::vector<int> eligible;     // frames t with t+1 in the shot, in order
     size_t next_eligible = 0;      // first eligible frame not yet examined
-    std::vector<Sample> analysed;
-    bool closed = false;
+    std::vector<Vote> analysed;
+    std::vector<int> reps;         // repeated-field flag of voters 1, 2, ...
+    int voters_seen = 0;           // voters among the eligible frames (decided by S_amm alone)
+    bool has_verdict = false;      // structure decided after samp_max_frames votes
+    ShotOut verdict{};
   };
-
   Status shot_step(MeasureStore& store, int avail, bool finished, std::vector<uint64_t>& need);
-  Status sampling_step(MeasureStore& store, Shot& sh, std::vector<uint64_t>& need);
+  Status sampling_step(MeasureStore& store, Shot& sh, std::vector<uint64_t>& need, bool& voted);
   int deep_check(MeasureStore& store, int t, int T, bool finished, int avail, std::vector<uint64_t>& need,
                  Status& st);
+  int deep_check_pulldown(MeasureStore& store, int t, int T, bool finished, int avail, std::vector<uint64_t>& need,
+                          Status& st);
+  bool wants_reps(const Shot& sh, size_t voter) const;
   void classify(const Shot& sh, ShotOut& out) const;
   void finish_clip();
 

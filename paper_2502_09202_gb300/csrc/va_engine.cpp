@@ -5,9 +5,11 @@
 #include <algorithm>
 #include <cmath>
 #include <chrono>
+#include <climits>
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <thread>
 
 namespace va {
 
@@ -79,6 +81,12 @@ static void hist_stats(const uint32_t* bins, int64_t n, analyser_frame_hist& h) 
   h.mad = mad;
 }
 
+int min_window(const analyser_params& p) {
+  // frames a deep check at t can still touch: t - kmax .. t + kmax + steady_span + steady_frames,
+  // and the oldest frame kept for the next check
+  return 2 * p.kmax + p.steady_span + p.steady_frames + 4;
+}
+
 int validate_params(const analyser_params& p, std::string& why) {
   if (p.levels < 2 || p.levels > 3) { why = "levels must be 2 or 3"; return ANALYSER_ERR_INVALID_ARG; }
   if (p.block != (kCoarseSide << (p.levels - 1))) {
@@ -95,9 +103,16 @@ int validate_params(const analyser_params& p, std::string& why) {
   if (p.jback < 1 || p.jback > 64) { why = "jback must be 1..64"; return ANALYSER_ERR_INVALID_ARG; }
   if (p.fast_window < 1 || p.fast_window > 1024) { why = "fast_window must be 1..1024"; return ANALYSER_ERR_INVALID_ARG; }
   if (p.samp_max_frames < 0 || p.samp_max_frames > 100000) { why = "samp_max_frames out of range"; return ANALYSER_ERR_INVALID_ARG; }
+  if (p.steady_frames < 1 || p.steady_frames > 64 || p.steady_span < 1 || p.steady_span > 8) {
+    why = "steady_frames must be 1..64 and steady_span 1..8";
+    return ANALYSER_ERR_INVALID_ARG;
+  }
+  if (p.rep_probe < 0 || p.rep_probe > 100000) { why = "rep_probe out of range"; return ANALYSER_ERR_INVALID_ARG; }
   if (!(p.fast_lambda >= 0) || !(p.fast_rise >= 0) || !(p.fast_tau >= 0) || !(p.deep_rho >= 0) || !(p.deep_tau >= 0) ||
+      !(p.done_eps >= 0) || !(p.steady_gamma >= 0) || !(p.lag_rho >= 0) || !(p.blend_ratio >= 0) ||
+      !(p.pd_rho >= 0) || !(p.pd_gamma_new >= 0) || !(p.pd_gamma_old >= 0) || !(p.rep_ratio >= 0) ||
       !(p.static_amm_px >= 0) || !(p.comb_ratio >= 0) || !(p.unequal_ratio >= 0) || !(p.pulldown_match >= 0) ||
-      !(p.kf_theta >= 0)) {
+      !(p.kf_theta >= 0) || !(p.wait_timeout_ms >= 0)) {
     why = "thresholds must be non-negative numbers";
     return ANALYSER_ERR_INVALID_ARG;
   }
@@ -117,8 +132,8 @@ int validate_params(const analyser_params& p, std::string& why) {
     why = "step_frames must be >= 0";
     return ANALYSER_ERR_INVALID_ARG;
   }
-  if (p.window_frames != 0 && p.window_frames < 2 * p.kmax + 6) {
-    why = "window_frames must be 0 (auto) or >= 2*kmax+6";
+  if (p.window_frames != 0 && p.window_frames < min_window(p)) {
+    why = "window_frames must be 0 (auto) or >= 2*kmax + steady_span + steady_frames + 4";
     return ANALYSER_ERR_INVALID_ARG;
   }
   return ANALYSER_OK;
@@ -185,6 +200,7 @@ Engine::~Engine() {
   for (cudaEvent_t& e : ev_) pool_release_event(e);
   pool_release_event(ev_chunk_);
   pool_release_event(ev_join_);
+  pool_release_event(ev_wait_);
   pool_release_stream(rstream);
   pool_release_stream(cstream);
   pool_release_stream(stream);
@@ -236,7 +252,7 @@ int Engine::add_clip(Clip* c, std::string& why, bool enlist) {
   c->p = p;
   c->want_vec_ = c->want_vec_ || (!c->stateless_ && p.want_motion);
   c->geo.init(c->geo.W, c->geo.H, p.levels, !c->external_l0);
-  if (c->cap <= 0) c->cap = p.window_frames > 0 ? p.window_frames : std::max(96, 2 * p.kmax + 8);
+  if (c->cap <= 0) c->cap = p.window_frames > 0 ? p.window_frames : std::max(96, min_window(p) + 2);
   c->l0.assign(c->cap, nullptr);
   c->l0_pitch.assign(c->cap, 0);
   const size_t bytes = ring_bytes(c->geo, c->cap);
@@ -297,6 +313,30 @@ void Engine::remove_clip(Clip* c) {
   }
 }
 
+cudaError_t Engine::wait_event(cudaEvent_t ev) {
+  if (!(p.wait_timeout_ms > 0)) return cudaEventSynchronize(ev);
+  // host watchdog: poll the event against a deadline instead of blocking in the driver
+  const double deadline = now_seconds() + 1e-3 * p.wait_timeout_ms;
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(ev);
+    if (e != cudaErrorNotReady) return e;
+    cudaGetLastError();
+    if (now_seconds() >= deadline) return cudaErrorTimeout;
+    std::this_thread::yield();
+  }
+}
+
+cudaError_t Engine::wait_stream(cudaStream_t st) {
+  if (!(p.wait_timeout_ms > 0)) return cudaStreamSynchronize(st);
+  if (!ev_wait_) {
+    const cudaError_t e = pool_event(&ev_wait_, false);
+    if (e != cudaSuccess) return e;
+  }
+  const cudaError_t e = cudaEventRecord(ev_wait_, st);
+  if (e != cudaSuccess) return e;
+  return wait_event(ev_wait_);
+}
+
 int Engine::upload_async(Clip* c, const uint8_t* frames, long long pitch, int nframes, int chunk) {
   const Geometry& g = c->geo;
   const int k = std::min(nframes, free_slots(c));
@@ -336,10 +376,15 @@ int Engine::poll_uploads(Clip* c, bool wait) {
   const int before = c->pushed;
   while (!c->up_chunks.empty()) {
     cudaEvent_t ev = c->up_chunks.front().second;
-    cudaError_t e = wait && c->pushed == before ? cudaEventSynchronize(ev) : cudaEventQuery(ev);
+    cudaError_t e = wait && c->pushed == before ? wait_event(ev) : cudaEventQuery(ev);
     if (e == cudaErrorNotReady) {
       cudaGetLastError();
       break;
+    }
+    if (e == cudaErrorTimeout) {
+      status = ANALYSER_ERR_TIMEOUT;
+      message = "frame copy not complete within wait_timeout_ms";
+      return -1;
     }
     if (e != cudaSuccess) {
       status = ANALYSER_ERR_CUDA;
@@ -848,7 +893,12 @@ int Engine::wave_complete() {
   };
   cudaError_t e;
   const double tw2 = now_seconds();
-  e = cudaStreamSynchronize(stream);
+  e = wait_stream(stream);
+  if (e == cudaErrorTimeout) {
+    status = ANALYSER_ERR_TIMEOUT;
+    message = "wave not complete within wait_timeout_ms";
+    return status;
+  }
   if (e) return fail(e, "cudaStreamSynchronize(wave)");
   const double tw3 = now_seconds();
   host_wait_ms += 1e3 * (tw3 - tw2);
@@ -944,8 +994,9 @@ int Engine::measure_pairs(int width, int height, const uint8_t* frames, long lon
     why = "null pointer or empty frame set";
     return ANALYSER_ERR_INVALID_ARG;
   }
-  if (pitch < width || pitch % 16 || ((uintptr_t)frames % 16) || stride % 16 || stride < pitch * height) {
-    why = "device frames need 16-byte aligned base, pitch and stride, pitch >= width";
+  if (pitch < width || pitch % 16 || pitch > INT_MAX / 2 || ((uintptr_t)frames % 16) || stride % 16 ||
+      stride < pitch * height) {
+    why = "device frames need 16-byte aligned base, pitch and stride, width <= pitch <= INT_MAX/2";
     return ANALYSER_ERR_INVALID_ARG;
   }
   for (int i = 0; i < npairs; i++) {

@@ -19,6 +19,7 @@ namespace va {
 
 double now_seconds();
 int validate_params(const analyser_params& p, std::string& why);
+int min_window(const analyser_params& p);   // smallest rolling window the detectors can work in
 int validate_size(int width, int height, const analyser_params& p, std::string& why);
 
 // Level geometry of one clip.
@@ -129,6 +130,11 @@ class Engine {
                     const int* kinds, const int* ia, const int* ib, int npairs, int64_t* records, int16_t* motion,
                     cudaStream_t st, std::string& why);
 
+  // waits for an event / all work queued on a stream, against params.wait_timeout_ms
+  // when it is set (cudaErrorTimeout when the deadline passes first)
+  cudaError_t wait_event(cudaEvent_t ev);
+  cudaError_t wait_stream(cudaStream_t st);
+
   // tile choice for a resolution (autotuned once per engine and size)
   void choose_tile(int width, int height, int* tbx, int* tby);
 
@@ -159,7 +165,7 @@ class Engine {
   int* h_status = nullptr;
   cudaEvent_t ev_[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaStream_t rstream = nullptr;   // refinement kernels of the split path
-  cudaEvent_t ev_chunk_ = nullptr, ev_join_ = nullptr;
+  cudaEvent_t ev_chunk_ = nullptr, ev_join_ = nullptr, ev_wait_ = nullptr;
   short2* d_cvec = nullptr;         // coarse vectors between the split kernels
   size_t cap_cvec = 0;
   // wave in flight (between wave_launch and wave_complete)

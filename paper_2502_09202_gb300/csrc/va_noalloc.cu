@@ -18,10 +18,14 @@
 //     streams) race on it; the accumulators and the status word are cleared at
 //     the start of every call;
 //   - the device address of the array is looked up once per device
-//     (cudaGetSymbolAddress) on the first call made with that device current;
-//     make that first call before any stream capture.
+//     (cudaGetSymbolAddress) by the first call for that device; make that
+//     first call before any stream capture;
+//   - every call waits for its stream before it returns (the record is read
+//     back to host memory), and leaves the calling thread's current device as
+//     it found it.
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -81,7 +85,9 @@ extern "C" int analyser_measure_pair_noalloc(const analyser_params* p, int width
   if (p->levels != 3 || p->block != 16 || p->radius_refine < 0 || p->radius_refine > 4 || p->mv_cost < 0 ||
       p->mv_cost > 64 || !pair_tile_supported(p->radius_coarse, p->tile_x ? p->tile_x : 8, p->tile_y ? p->tile_y : 4))
     return ANALYSER_ERR_INVALID_ARG;
-  if (pitch_bytes < width || pitch_bytes % 16 || ((uintptr_t)frame_a % 16) || ((uintptr_t)frame_b % 16))
+  // field kinds double the pitch, and the kernels' plane descriptors hold it in an int
+  if (pitch_bytes < width || pitch_bytes % 16 || pitch_bytes > INT_MAX / 2 || ((uintptr_t)frame_a % 16) ||
+      ((uintptr_t)frame_b % 16))
     return ANALYSER_ERR_INVALID_ARG;
 
   // image geometry of this pair kind: a frame, or a field (pitch doubled)
@@ -112,7 +118,14 @@ extern "C" int analyser_measure_pair_noalloc(const analyser_params* p, int width
   const size_t off_j2 = off; off = align_up(off + (size_t)p2 * h2 + 16, 256);
   if (off > kNoAllocScratchBytes) return ANALYSER_ERR_INVALID_ARG;   // beyond the fixed scratch
 
-  if (cudaSetDevice(p->device) != cudaSuccess) return ANALYSER_ERR_CUDA;
+  int prev_device = 0;
+  if (cudaGetDevice(&prev_device) != cudaSuccess) return ANALYSER_ERR_CUDA;
+  if (prev_device != p->device && cudaSetDevice(p->device) != cudaSuccess) return ANALYSER_ERR_CUDA;
+  // the caller's current device is restored on every return below
+  struct RestoreDevice {
+    int dev, was;
+    ~RestoreDevice() { if (dev != was) cudaSetDevice(was); }
+  } restore{p->device, prev_device};
   unsigned char* s = nullptr;
   int rc = scratch_ptr(p->device, &s);
   if (rc) return rc;

@@ -26,13 +26,18 @@ class Params(ctypes.Structure):
         ("mv_cost", c_int),
         ("kmax", c_int), ("jback", c_int), ("fast_window", c_int),
         ("fast_lambda", c_double), ("fast_rise", c_double), ("fast_tau", c_double), ("deep_rho", c_double), ("deep_tau", c_double),
+        ("done_eps", c_double), ("steady_gamma", c_double), ("steady_frames", c_int), ("steady_span", c_int),
+        ("lag_rho", c_double), ("blend_ratio", c_double),
+        ("pd_rho", c_double), ("pd_gamma_new", c_double), ("pd_gamma_old", c_double),
         ("samp_max_frames", c_int),
         ("static_amm_px", c_double), ("comb_ratio", c_double), ("unequal_ratio", c_double),
+        ("rep_ratio", c_double), ("rep_probe", c_int),
         ("pulldown_match", c_double),
         ("kf_theta", c_double),
         ("device", c_int), ("window_frames", c_int), ("mem_budget_bytes", c_ull), ("want_motion", c_int),
         ("tile_x", c_int), ("tile_y", c_int), ("time_kernels", c_int),
         ("step_frames", c_int), ("kernel_mode", c_int), ("want_histogram", c_int),
+        ("wait_timeout_ms", c_double),
     ]
 
 

@@ -117,7 +117,7 @@ def test_small_clip_device_push_and_small_window():
     api = _api()
     spec = synth.config_small()
     frames = synth.Clip(spec).frames()
-    with api.Analyser(spec.width, spec.height, spec.fps, window_frames=22) as a:
+    with api.Analyser(spec.width, spec.height, spec.fps, window_frames=26) as a:
         a.push_device(_dev(frames))
         a.finish()
         got = a.results()
@@ -207,7 +207,7 @@ def test_long_clip_streams_through_a_small_window():
     frames = synth.Clip(spec).frames()
     ref = OA.analyse_frames(frames)
     for chunks in ((260,), (7, 100, 1, 152)):
-        with api.Analyser(spec.width, spec.height, spec.fps, window_frames=24) as a:
+        with api.Analyser(spec.width, spec.height, spec.fps, window_frames=26) as a:
             s = 0
             for c in chunks:
                 a.push(frames[s:s + c])
@@ -226,7 +226,7 @@ def test_long_clip_device_pushes_any_window():
     frames = synth.Clip(spec).frames()
     ref = OA.analyse_frames(frames)
     dev = _dev(frames)
-    for window in (24, 64, 128, 300):
+    for window in (26, 64, 128, 300):
         for chunks in ((260,), (7, 100, 1, 152)):
             with api.Analyser(spec.width, spec.height, spec.fps, window_frames=window) as a:
                 s = 0
@@ -291,7 +291,7 @@ def test_frame_histograms_match_the_oracle():
     api = _api()
     spec = synth.config_small()
     frames = synth.Clip(spec).frames()
-    with api.Analyser(spec.width, spec.height, spec.fps, want_histogram=1, window_frames=24) as a:
+    with api.Analyser(spec.width, spec.height, spec.fps, want_histogram=1, window_frames=26) as a:
         a.push(frames)
         a.finish()
         got = a.results()
@@ -324,3 +324,27 @@ def test_largest_accepted_frame_size():
         assert np.array_equal(mot[k], vec)
     with pytest.raises(api.AnalyserError):
         api.Analyser(w + 2, h, 25.0)
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+@pytest.mark.parametrize("radius", [8, 16, 24])
+@pytest.mark.parametrize("refine", [0, 1, 2, 4])
+@pytest.mark.parametrize("lam", [0, 4, 64])
+def test_every_accepted_search_parameter_matches_the_oracle(levels, radius, refine, lam):
+    """Every estimator parameter the C ABI accepts (levels 2-3, coarse radius
+    8/16/24, refinement radius 0-4, motion cost 0-64), on pairs of every kind at a
+    ragged size: records and motion fields element by element against the oracle.
+    Radius 2 with 3 levels runs the split coarse/refinement kernels, everything
+    else the fused kernel's general refinement."""
+    api = _api()
+    w, h = 232, 152
+    spec = synth.config_interlaced(nframes=4, width=w, height=h)
+    frames = synth.Clip(spec).frames()
+    sp = OM.SearchParams(levels=levels, block=4 << (levels - 1), radius=radius, refine=refine, mv_cost=lam)
+    kinds, ia, ib = [0, 1, 2, 3, 4, 0], [0, 1, 1, 2, 3, 3], [1, 1, 2, 3, 3, 0]
+    rec, mot = api.measure_pairs(_dev(frames), kinds, ia, ib, want_motion=True, levels=levels,
+                                 block=4 << (levels - 1), radius_coarse=radius, radius_refine=refine, mv_cost=lam)
+    for k in range(len(kinds)):
+        ref, vec = _oracle_pair(kinds[k], frames[ia[k]], frames[ib[k]], sp)
+        assert list(rec[k]) == [ref[f] for f in REC7], (k, kinds[k])
+        assert np.array_equal(mot[k], vec), (k, kinds[k])

@@ -72,6 +72,42 @@ def test_defaults_and_validation_without_a_gpu(native):
     native.lib.analyser_destroy(None)
 
 
+def test_budget_below_need_is_refused_before_device_work(native):
+    # the 1080p window of 96 frames needs ~330 MB: a 1 MB budget is refused with
+    # ANALYSER_ERR_OOM from the sizes alone (no GPU here), an unset one is not
+    # refused for that reason
+    h = ctypes.c_void_p()
+    p = native.default_params(mem_budget_bytes=1 << 20)
+    assert native.lib.analyser_create(1920, 1080, 25.0, ctypes.byref(p), ctypes.byref(h)) == native.ERR_OOM
+    assert not h.value
+    p = native.default_params(wait_timeout_ms=-1.0)
+    assert native.lib.analyser_create(1920, 1080, 25.0, ctypes.byref(p), ctypes.byref(h)) == native.ERR_INVALID_ARG
+    p = native.default_params(window_frames=25)      # below 2*kmax + steady_span + steady_frames + 4
+    assert native.lib.analyser_create(320, 180, 25.0, ctypes.byref(p), ctypes.byref(h)) == native.ERR_INVALID_ARG
+
+
+def test_offline_handle_refuses_frames(native):
+    from paper_2502_09202_gb300 import api
+    frames = synth.Clip(synth.config_small()).frames(0, 6)
+    o = OA.OracleAnalyser(lambda t: frames[t], 6)
+    o.run()
+
+    def get(kind, a, b):
+        m = o.m(kind, a, b)
+        return [m[k] for k in OM.REC_FIELDS]
+
+    h = ctypes.c_void_p()
+    p = native.default_params()
+    fn = native.MEASURE_FN(lambda ctx, kind, a, b, rec: [rec.__setitem__(i, v) for i, v in enumerate(get(kind, a, b))]
+                           and 0)
+    assert native.lib.analyser_detect_offline(ctypes.byref(p), 320, 180, 6, fn, None, ctypes.byref(h)) == native.OK
+    buf = np.zeros((180, 320), np.uint8)
+    assert native.lib.analyser_push_frames(h, buf.ctypes.data, 320, 1) == native.ERR_STATE
+    r = native.Results()
+    assert native.lib.analyser_results(h, ctypes.byref(r)) == native.OK     # a refused push is not sticky here
+    native.lib.analyser_destroy(h)
+
+
 def _offline(frames, params=OA.Params()):
     from paper_2502_09202_gb300 import api
     o = OA.OracleAnalyser(lambda t: frames[t], len(frames), params)
@@ -123,9 +159,10 @@ def test_offline_callback_errors_surface(native):
 # ---- the library's detectors on scripted records ---------------------------------
 # A record with S_i = S_j = S_ij = 0 and S_ii = S_jj = 1 has C = 0 and Vi, Vj > 0,
 # so NCC = 0 and SWR = 1, and S_amm = ACT^2 * 65536 * nb makes ACT = sqrt(AMM) the
-# scripted value.  The expected decisions are derived by hand from the rules
-# (Sec. III.B-D), as in the oracle's detector pins; the oracle run on the same
-# records must agree on everything.
+# scripted value (and AMM = ACT^2, the motion part the structure rules read).  The
+# expected decisions are derived by hand from the rules (Sec. III.B-D), as in the
+# oracle's detector pins; the oracle run on the same records must agree on
+# everything, the reported measure set included.
 
 def _scripted_record(act, kind, a, b):
     n, nb = (64 * 64, 16) if kind == OM.FRAME else (64 * 32, 8)
@@ -143,20 +180,17 @@ def _both(T, act):
     got = api.detect_offline(64, 64, T, get)
 
     class Records(OA.OracleAnalyser):
-        def m(self, kind, a, b):
-            key = (kind, a, b)
-            if key not in self.cache:
-                self.cache[key] = OM.finalise(dict(zip(OM.REC_FIELDS, get(kind, a, b))))
-            return self.cache[key]
+        def _measure(self, kind, a, b):
+            return OM.finalise(dict(zip(OM.REC_FIELDS, get(kind, a, b))))
 
     ref = Records(lambda t: np.zeros((64, 64), np.uint8), T).run()
     _same(got, ref)
     return got
 
 
-def _positions(p, field_act=1.0):
+def _positions(p, g=0.0, field_act=1.0):
     def act(kind, a, b):
-        return 1.0 + 9.0 * abs(p(a) - p(b)) if kind == OM.FRAME else field_act
+        return 1.0 + g * abs(a - b) + 9.0 * abs(p(a) - p(b)) if kind == OM.FRAME else field_act
     return act
 
 
@@ -176,13 +210,33 @@ def test_library_dissolve_on_scripted_records(native):
     r = _both(20, _positions(lambda f: 0.0 if f <= 10 else p.get(f, 1.0)))
     assert r["dissolves"] == [(10, 3)] and r["cuts"] == []
     assert r["keyframes"] == [0, 9, 13]
-    assert _requested(r) == [(10, 8), (10, 9), (10, 12), (10, 13), (10, 14)]
+    assert _requested(r) == [(10, 7), (10, 8), (10, 9), (10, 12), (10, 13), (10, 14)]
+
+
+def test_library_completion_and_steadiness_on_scripted_records(native):
+    # frame 12 farther from 10 than frame 11: K = 1 incomplete, dissolve (10, 3)
+    p = {11: 0.5, 12: 0.66}
+    assert _both(20, _positions(lambda f: 0.0 if f <= 10 else p.get(f, 1.0)))["dissolves"] == [(10, 3)]
+    # the new shot still moves at 12: K = 2 not steady, dissolve (10, 3)
+    p = {11: 0.5, 12: 1.0}
+    assert _both(24, _positions(lambda f: 0.0 if f <= 10 else p.get(f, 1.1)))["dissolves"] == [(10, 3)]
 
 
 def test_library_ramp_start_on_scripted_records(native):
-    steps = {11: 0.5 / 9, 12: 1.3 / 9, 13: 2.4 / 9}
+    steps = {11: 0.1, 12: 0.35, 13: 0.65}
     r = _both(20, _positions(lambda f: 0.0 if f <= 10 else steps.get(f, 1.0)))
     assert r["dissolves"] == [(10, 4)] and r["cuts"] == []
+    assert _requested(r) == [(10, 6), (10, 8), (10, 9), (10, 12), (10, 13), (10, 14), (10, 15)]
+
+
+def test_library_lag_and_blend_tests_on_scripted_records(native):
+    # a flash at 11 in a shot whose ACT grows by 0.45 per frame of distance: K = 8 passes
+    # (a)-(c) but ACT(10,18) = 4.6 is not above 1.5 * ACT(10,2) = 6.9
+    r = _both(30, _positions(lambda f: 1.0 if f == 11 else 0.0, g=0.45))
+    assert r["cuts"] == [] and r["dissolves"] == [] and (OM.FRAME, 10, 2) in r["measures"]
+    # an abrupt change at 16 after frames of growing distance: a hardcut, no dissolve
+    r = _both(30, _positions(lambda f: 0.0 if f <= 15 else 1.0, g=0.3))
+    assert r["cuts"] == [16] and r["dissolves"] == []
 
 
 def test_library_keyframes_on_scripted_records(native):
@@ -190,18 +244,23 @@ def test_library_keyframes_on_scripted_records(native):
 
 
 @pytest.mark.parametrize("v,label,fo", [
-    ((5.0, 6.0, 3.0), OA.INTERLACED, OA.FO_TFF),
-    ((5.0, 3.0, 6.0), OA.INTERLACED, OA.FO_BFF),
-    ((5.0, 3.0, 3.0), OA.PROGRESSIVE, OA.FO_NONE),
+    ((1.0, 3.0, 1.0), OA.INTERLACED, OA.FO_TFF),
+    ((1.0, 1.0, 3.0), OA.INTERLACED, OA.FO_BFF),
+    ((1.0, 1.0, 1.0), OA.PROGRESSIVE, OA.FO_NONE),
+    ((0.55, 1.4, 1.0), OA.PROGRESSIVE, OA.FO_NONE),
     ((0.1, 1.0, 1.0), OA.PROGRESSIVE, OA.FO_NONE),
 ])
 def test_library_structure_on_scripted_records(native, v, label, fo):
+    # field ACT v -> AMM v^2 (SWR = 1): (1, 9, 1) combed and B = 9: TFF; (1, 1, 9): BFF;
+    # (1, 1, 1) combed but B = 1; (0.3025, 1.96, 1): B = 1.96 but A0 < 0.65 * 1; (0.01, 1, 1)
     def act(kind, a, b):
         if kind == OM.FRAME:
             return 1.0                      # AMM = 1 px: not static
         if kind == OM.UPPER_LOWER:
             return v[0] if a == b else v[1]
-        return v[2]
+        if kind == OM.LOWER_UPPER:
+            return v[2]
+        return 1.0                          # same-parity pairs: no repeated field
     r = _both(30, act)
     assert (r["label"], r["field_order"]) == (label, fo)
 
@@ -209,13 +268,37 @@ def test_library_structure_on_scripted_records(native, v, label, fo):
 @pytest.mark.parametrize("phase", [0, 2, 3])
 def test_library_pulldown_phase_on_scripted_records(native, phase):
     def act(kind, a, b):
-        if kind == OM.FRAME:
-            return 1.0
-        if kind == OM.UPPER_LOWER and a == b:
-            return 5.0 if (a - phase) % 5 in (2, 3) else 0.1
+        c = (a - phase) % 5
+        if kind == OM.UPPER_UPPER:
+            return 0.0 if c == 1 else 1.0
+        if kind == OM.LOWER_LOWER:
+            return 0.0 if c == 3 else 1.0
         return 1.0
     r = _both(30, act)
     assert (r["label"], r["pulldown_phase"]) == (OA.PULLDOWN, phase)
+
+
+def test_library_pulldown_shot_cut_on_scripted_records(native):
+    # phase-0 cadence (peaks of 3 at positions 1 and 3), voters 0..19, a cut at 40
+    # (a_39 = 3 against a_34 = 1) and a flash at 29 that the old-shot test rejects
+    def act(kind, a, b):
+        if kind == OM.FRAME:
+            if b == a + 1:
+                if a in (28, 29):
+                    return 9.0
+                if a == 39:
+                    return 3.0
+                return 3.0 if a % 5 in (1, 3) else 1.0
+            return 10.0 if (a < 40) != (b < 40) else 2.0
+        if kind == OM.UPPER_UPPER:
+            return 0.0 if a % 5 == 1 else 1.0
+        if kind == OM.LOWER_LOWER:
+            return 0.0 if a % 5 == 3 else 1.0
+        return 1.0
+    r = _both(60, act)
+    assert r["cuts"] == [40] and r["dissolves"] == []
+    assert (r["label"], r["pulldown_phase"]) == (OA.PULLDOWN, 0)
+    assert [p for p in _requested(r) if 20 <= p[0] <= 39] == []
 
 
 def test_missing_library_fails_loudly(tmp_path):

@@ -42,10 +42,34 @@ def test_noalloc_matches_measure_pairs_on_consecutive_calls():
     p = N.default_params()
     calls = [(0, 0, 1), (1, 2, 3), (2, 1, 2), (0, 3, 0), (3, 1, 2), (4, 0, 3)]
     want, _ = api.measure_pairs(view, [c[0] for c in calls], [c[1] for c in calls], [c[2] for c in calls])
-    # two calls in a row (and two more): each equals the allocating entry point, exactly
+    # one warm call loads the kernels; after it, no call may take device memory:
+    # neither CUDA's free bytes nor the library's resource cache may change
+    _noalloc(N, p, spec.width, spec.height, 0, buf, 0, 1)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    cached0 = N.lib.analyser_cached_bytes()
+    # two calls in a row (and four more): each equals the allocating entry point, exactly
+    got = [_noalloc(N, p, spec.width, spec.height, kind, buf, a, b) for kind, a, b in calls]
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert N.lib.analyser_cached_bytes() == cached0
     for k, (kind, a, b) in enumerate(calls):
-        got = _noalloc(N, p, spec.width, spec.height, kind, buf, a, b)
-        assert got == [int(x) for x in want[k]], (kind, a, b)
+        assert got[k] == [int(x) for x in want[k]], (kind, a, b)
+
+
+def test_noalloc_keeps_the_callers_device_and_checks_the_pitch():
+    from paper_2502_09202_gb300 import native as N
+    frames = synth.Clip(synth.config_small()).frames(0, 2)
+    buf = _dev(frames)
+    p = N.default_params()
+    before = torch.cuda.current_device()
+    _noalloc(N, p, 320, 180, 0, buf, 0, 1)
+    assert torch.cuda.current_device() == before
+    rec = (ctypes.c_int64 * 7)()
+    # a pitch whose doubled field pitch would not fit the kernels' int descriptors is refused
+    code = N.lib.analyser_measure_pair_noalloc(ctypes.byref(p), 320, 180, 1, buf[0].data_ptr(), buf[1].data_ptr(),
+                                               1 << 30, rec, None)
+    assert code == N.ERR_INVALID_ARG
 
 
 def test_noalloc_repeat_and_size_limit():
