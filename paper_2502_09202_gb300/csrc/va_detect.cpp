@@ -125,7 +125,6 @@ int Detector::deep_check(MeasureStore& store, int t, int T, bool finished, int a
     for (int K2 = K0; K2 <= p_.kmax && t + K2 + 1 < avail; K2++) {
       std::vector<uint64_t> more;
       deep_pairs(t, K2, s0, p_.jback, more);
-      if (K2 >= 2 && t - K2 >= s0) more.push_back(pair_key(kFrame, t, t - K2));
       for (uint64_t k : more)
         if (!store.find(key_kind(k), key_a(k), key_b(k))) need.push_back(k);
     }
@@ -190,7 +189,11 @@ int Detector::deep_check(MeasureStore& store, int t, int T, bool finished, int a
       if (!steady) continue;
       if (t - K >= s0) {                                                   // (d)
         Measure* lag = store.find(kFrame, t, t - K);
-        if (!lag) return request_from(K);
+        if (!lag) {   // read only once (a)-(c) hold: not requested ahead
+          need.push_back(pair_key(kFrame, t, t - K));
+          st = kNeedPairs;
+          return 0;
+        }
         lag->used = true;
         const double lr = p_.lag_rho * lag->act;
         if (!(x > lr)) return 0;

@@ -8,11 +8,14 @@ namespace va {
 // packed-byte primitives
 // ---------------------------------------------------------------------------
 
-// c + sum over the 4 bytes of |a_k - b_k|
+// c + sum over the 4 bytes of |a_k - b_k|.  PTX vabsdiff4 with accumulate is
+// the fastest packed sequence measured on GB300 in register-only loops whose
+// operands cannot be shared or hoisted (75 T |a-b|/s against 53 for the sum of
+// absolute differences intrinsic plus an add and 47 for vabsdiff4 + dp4a; mixing
+// sequences across chains gains nothing), and in the pair kernels (8.5 against
+// 9.3 us per 1080p frame pair).  VA_SAD_VSAD builds the intrinsic variant.
 __device__ __forceinline__ uint32_t sad4(uint32_t a, uint32_t b, uint32_t c) {
-#if defined(VA_SAD_DP4A)
-  return __dp4a(__vabsdiffu4(a, b), 0x01010101u, c);
-#elif defined(VA_SAD_VSAD)
+#if defined(VA_SAD_VSAD)
   return __vsadu4(a, b) + c;
 #else
   uint32_t d;
@@ -256,7 +259,7 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
 // multiplier that is not a power of two makes the key one integer multiply-add,
 // which runs beside the SAD instructions instead of on their pipe.  Keys stay
 // below 2^32 for cost <= 16*255 + 64*2*24.
-constexpr uint32_t kCoarseKeyM = (1u << 18) + 1u;
+constexpr uint32_t kCoarseKeyM = kCoarseKeyMul;
 
 // Rows of the coarse search for one block and NJ consecutive vx candidates
 // starting at vx0: slides down the staged window rows from `wrow` (the block's
@@ -265,7 +268,7 @@ constexpr uint32_t kCoarseKeyM = (1u << 18) + 1u;
 // rows shifted by j bytes; otherwise the shifts are taken here.
 template <int R, int NJ, int WWORDS, int COPY, bool SHIFTED>
 __device__ __forceinline__ uint32_t coarse_rows(const uint32_t* wrow, uint32_t i0, uint32_t i1, uint32_t i2,
-                                                uint32_t i3, int vx0, uint32_t lamM) {
+                                                uint32_t i3, int vx0, uint32_t lamM, uint32_t keyM) {
   // acc[j][c & 3] holds candidate c = dy - k (vy = c - R): it receives row k
   // of the block at window row dy, starts at k = 0 and completes at k = 3.
   uint32_t acc[NJ][4];
@@ -301,9 +304,16 @@ __device__ __forceinline__ uint32_t coarse_rows(const uint32_t* wrow, uint32_t i
       const uint32_t bv = lamM * (uint32_t)avy + (((uint32_t)avy << 12) | ((uint32_t)(vy + R) << 6));
 #pragma unroll
       for (int j = 0; j < NJ; j++) {
-        const uint32_t key = acc[j][(dy - 3) & 3] * kCoarseKeyM + bv;
+        const uint32_t key = acc[j][(dy - 3) & 3] * keyM + bv;
+#if defined(VA_COARSE_NOPEND)
+        best[j] = min(best[j], key);
+#elif defined(VA_COARSE_MIN2)
+        if (((dy - 3) & 1) == 0 && dy < 2 * R + 3) pend[j] = key;
+        else best[j] = min(best[j], min(pend[j], key));
+#else
         if (((dy - 3) & 1) == 0 && dy < 2 * R + 3) pend[j] = key;
         else best[j] = __vimin3_u32(best[j], pend[j], key);
+#endif
       }
     }
   }
@@ -327,7 +337,8 @@ __device__ __forceinline__ uint32_t coarse_rows(const uint32_t* wrow, uint32_t i
 // s_vx/s_vy (after a barrier).
 template <int R, int TBX, int TBY, int NT, bool SHIFTED>
 __device__ __forceinline__ void coarse_phase(const uint32_t* jwin, const uint32_t* iwin, int bx0, int by0, int nbx,
-                                             int nby, int lam, uint32_t* s_best32, int* s_vx, int* s_vy, int tid) {
+                                             int nby, int lam, uint32_t keyM, uint32_t* s_best32, int* s_vx, int* s_vy,
+                                             int tid) {
   constexpr int GQ = R / 2, NB = TBX * TBY, NG = NB * GQ, WWORDS = TBX + GQ + 1;
   constexpr int COPY = (TBY * 4 + 2 * R) * WWORDS;
   static_assert(R % 4 == 0 && NG % 32 == 0 && NT >= NG + NB, "coarse thread layout");
@@ -338,13 +349,13 @@ __device__ __forceinline__ void coarse_phase(const uint32_t* jwin, const uint32_
   const bool active = (grouped || last) && (bx0 + bxl < nbx) && (by0 + byl < nby);
   const uint32_t i0 = iwin[(byl * 4 + 0) * TBX + bxl], i1 = iwin[(byl * 4 + 1) * TBX + bxl];
   const uint32_t i2 = iwin[(byl * 4 + 2) * TBX + bxl], i3 = iwin[(byl * 4 + 3) * TBX + bxl];
-  const uint32_t lamM = (uint32_t)lam * kCoarseKeyM;
+  const uint32_t lamM = (uint32_t)lam * keyM;
   const uint32_t* wrow = jwin + (byl * 4) * WWORDS + bxl + g;
   uint32_t tbest = 0xFFFFFFFFu;
   if (grouped)   // warp-uniform
-    tbest = coarse_rows<R, 4, WWORDS, COPY, SHIFTED>(wrow, i0, i1, i2, i3, -R + 4 * g, lamM);
+    tbest = coarse_rows<R, 4, WWORDS, COPY, SHIFTED>(wrow, i0, i1, i2, i3, -R + 4 * g, lamM, keyM);
   else if (tid < ((NG + NB + 31) & ~31))
-    tbest = coarse_rows<R, 1, WWORDS, COPY, SHIFTED>(wrow, i0, i1, i2, i3, R, lamM);
+    tbest = coarse_rows<R, 1, WWORDS, COPY, SHIFTED>(wrow, i0, i1, i2, i3, R, lamM, keyM);
   if (active) atomicMin(&s_best32[bl], tbest);
   __syncthreads();
   for (int i = tid; i < NB; i += NT) {

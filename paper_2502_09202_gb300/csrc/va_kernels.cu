@@ -365,7 +365,8 @@ pair_kernel(const PairBatch b) {
       for (int i = tid; i < NB; i += NT) s_best32[i] = 0xFFFFFFFFu;
       __syncthreads();
 
-      coarse_phase<R, TBX, TBY, NT, false>(jwin, iwin, bx0, by0, nbx, nby, lam, s_best32, s_vx, s_vy, tid);
+      coarse_phase<R, TBX, TBY, NT, false>(jwin, iwin, bx0, by0, nbx, nby, lam, b.cfg.key_mul, s_best32, s_vx, s_vy,
+                                             tid);
     }
 
     // ---- phase B: refinement at levels L-2 .. 0 -------------------------------

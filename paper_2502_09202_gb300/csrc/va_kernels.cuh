@@ -49,11 +49,18 @@ struct PairJob {
   short2* cvec;              // coarse vectors (nby*nbx) between the split kernels, or null
 };
 
+// Multiplier of the coarse candidate keys (see coarse_rows in va_device.cuh);
+// the kernels read it from their launch parameters, so that the key stays one
+// integer multiply-add instead of the shift-and-add sequence a compile-time
+// 2^18 + 1 turns into on the integer ALU pipe the packed SADs use.
+constexpr uint32_t kCoarseKeyMul = (1u << 18) + 1u;
+
 struct SearchCfg {
   int levels;    // L; level-0 block side is kCoarseSide << (L-1)
   int radius;    // coarse exhaustive radius R (multiple of 4)
   int refine;    // refinement radius r
   int lambda;    // motion cost per pixel of |vx|+|vy|
+  uint32_t key_mul = kCoarseKeyMul;   // always kCoarseKeyMul
 };
 
 struct PairBatch {

@@ -1,31 +1,35 @@
-// Register-only throughput of the packed-SAD instruction the kernels use
-// (vabsdiff4 with accumulate): the denominator of the ALU roofline.
+// Register-only throughput of the packed-SAD step the kernels use (sad4 in
+// va_device.cuh): the denominator of the ALU roofline.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
 #include "../../include/analyser.h"
+#include "va_device.cuh"
 
 namespace {
 
 __global__ void sad_peak_kernel(uint32_t* out, int iters, uint32_t seed) {
-  uint32_t a[8], acc[8];
+  // 8 accumulator chains x 16 operands: the 128 (a, b) pairs of an iteration are
+  // distinct and every b changes each iteration, so no SAD can be shared with
+  // another or hoisted out of the loop (16 adds per 128 SADs is the only other
+  // work, which makes the figure a slight underestimate of the peak)
+  uint32_t a[8], acc[8], bw[16];
 #pragma unroll
   for (int i = 0; i < 8; i++) {
     a[i] = seed * (threadIdx.x + 7u * i + 1u);
     acc[i] = 0;
   }
-  uint32_t b = seed ^ blockIdx.x;
+#pragma unroll
+  for (int u = 0; u < 16; u++) bw[u] = (seed ^ blockIdx.x) * (2u * u + 1u);
   for (int it = 0; it < iters; it++) {
-    // 128 packed SADs per iteration (asm volatile: none is folded away); the
-    // only other work is the loop counter and one add
 #pragma unroll
     for (int u = 0; u < 16; u++) {
 #pragma unroll
-      for (int i = 0; i < 8; i++)
-        asm volatile("vabsdiff4.u32.u32.u32.add %0, %1, %2, %3;" : "=r"(acc[i]) : "r"(a[i]), "r"(b), "r"(acc[i]));
+      for (int i = 0; i < 8; i++) acc[i] = va::sad4(a[i], bw[u], acc[i]);
     }
-    b += 0x01030507u;
+#pragma unroll
+    for (int u = 0; u < 16; u++) bw[u] += 0x01030507u;
   }
   uint32_t s = 0;
 #pragma unroll

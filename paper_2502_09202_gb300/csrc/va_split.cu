@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(CoarseShape<R, TBX, TBY>::NT, CoarseShape<R, T
   }
   for (int i = tid; i < NB; i += NT) s_best32[i] = 0xFFFFFFFFu;
   __syncthreads();
-  coarse_phase<R, TBX, TBY, NT, true>(s_jwin, s_iw, bx0, by0, nbx, nby, b.cfg.lambda, s_best32, s_vx, s_vy, tid);
+  coarse_phase<R, TBX, TBY, NT, true>(s_jwin, s_iw, bx0, by0, nbx, nby, b.cfg.lambda, b.cfg.key_mul, s_best32, s_vx,
+                                       s_vy, tid);
   for (int i = tid; i < NB; i += NT) {
     const int bx = bx0 + i % TBX, by = by0 + i / TBX;
     if (bx < nbx && by < nby) jb.cvec[(size_t)by * nbx + bx] = make_short2((short)s_vx[i], (short)s_vy[i]);
