@@ -119,6 +119,9 @@ typedef struct {
                                           estimator (levels 3, radius_refine 2), fused otherwise;
                                           1: always the fused kernel (0) */
   int want_histogram;                  /* per-frame luma histogram and its statistics (0) */
+  int prefetch_frames;                 /* when the detectors wait for pairs, a look-ahead over at most
+                                          this many frames asks for the pairs they will read next
+                                          (computed in the same wave; decisions unchanged) (256) */
   double wait_timeout_ms;              /* host watchdog: a wave or frame copy not complete after this
                                           many ms fails the call with ANALYSER_ERR_TIMEOUT (sticky);
                                           0 = wait without a limit (0) */
@@ -333,8 +336,12 @@ int server_poll(server* s, long long ticket, analyser_results_t* out);
 /*
  * One scheduling step: admit queued clips while the budget allows, copy the
  * next frames of every admitted clip into its window, run one GPU wave over
- * all of them and retire finished clips.  *active (optional) receives the
- * number of clips admitted or queued after the step.
+ * all of them and retire finished clips.  Admission takes queued clips in
+ * arrival order and admits every one whose window fits what is left of the
+ * budget, so a large clip waiting for memory does not hold back smaller ones
+ * behind it; once the oldest queued clip has waited 0.5 s, nothing behind it
+ * is admitted before it.  *active (optional) receives the number of clips
+ * admitted or queued after the step.
  */
 int server_step(server* s, int* active);
 

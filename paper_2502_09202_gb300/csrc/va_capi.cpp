@@ -129,6 +129,7 @@ int analyser_default_params(analyser_params* p) {
   p->step_frames = 32;
   p->kernel_mode = 0;
   p->want_histogram = 0;
+  p->prefetch_frames = 256;
   p->wait_timeout_ms = 0.0;
   return ANALYSER_OK;
 }
@@ -424,17 +425,30 @@ int server_step(server* s, int* active) {
   if (!s) return ANALYSER_ERR_INVALID_ARG;
   if (s->status) return s->status;
   va::Engine& e = *s->eng;
-  // admission: first come, first served, while the budget allows
-  while (!s->queue.empty()) {
-    server::Req& r = s->reqs[s->queue.front()];
-    if (s->budget && s->used + r.bytes > s->budget) break;
-    std::string why;
-    const int rc = e.add_clip(r.clip.get(), why);
-    if (rc == ANALYSER_ERR_OOM && !e.clips.empty()) break;   // retry when memory frees up
-    if (rc) return fail_srv(s, rc, why);
-    r.admitted = true;
-    s->used += r.bytes;
-    s->queue.pop_front();
+  // admission in arrival order of every queued clip whose window fits what is
+  // left of the budget: a clip too large for the space free now does not hold
+  // back smaller ones behind it, unless it has waited kHeadWaitS already, in
+  // which case nothing behind it is admitted until it is
+  constexpr double kHeadWaitS = 0.5;
+  const double now = va::now_seconds();
+  for (auto it = s->queue.begin(); it != s->queue.end();) {
+    server::Req& r = s->reqs[*it];
+    const bool head = it == s->queue.begin();
+    bool admit = !(s->budget && s->used + r.bytes > s->budget);
+    if (admit) {
+      std::string why;
+      const int rc = e.add_clip(r.clip.get(), why);
+      if (rc == ANALYSER_ERR_OOM && !e.clips.empty()) admit = false;   // retry when memory frees up
+      else if (rc) return fail_srv(s, rc, why);
+    }
+    if (admit) {
+      r.admitted = true;
+      s->used += r.bytes;
+      it = s->queue.erase(it);
+      continue;
+    }
+    if (head && now - r.t_submit > kHeadWaitS) break;
+    ++it;
   }
   // top up every admitted clip's window with asynchronous chunked copies (at
   // most step_frames new frames per clip and step, so that short clips arriving

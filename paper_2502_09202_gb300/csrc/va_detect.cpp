@@ -147,14 +147,14 @@ int Detector::deep_check(MeasureStore& store, int t, int T, bool finished, int a
     for (int j = 1; j <= p_.jback; j++) {
       if (t - j < s0) continue;
       Measure* m = store.find(kFrame, t, t - j);
-      m->used = true;
+      use(m);
       if (!have_ref || m->act > ref) ref = m->act;
       have_ref = true;
     }
     Measure* fk = store.find(kFrame, t, t + K);
     Measure* fk1 = store.find(kFrame, t, t + K + 1);
     Measure* af = store.find(kFrame, t + K, t + K + 1);
-    fk->used = fk1->used = af->used = true;
+    use(fk); use(fk1); use(af);
     const double x = fk->act, x1 = fk1->act;
     const double base = p_.deep_rho * ref + p_.deep_tau;
     const double after = p_.deep_rho * af->act + p_.deep_tau;
@@ -194,12 +194,12 @@ int Detector::deep_check(MeasureStore& store, int t, int T, bool finished, int a
           st = kNeedPairs;
           return 0;
         }
-        lag->used = true;
+        use(lag);
         const double lr = p_.lag_rho * lag->act;
         if (!(x > lr)) return 0;
       }
       Measure* prev = store.find(kFrame, t, t + K - 1);                    // (e), read by hypothesis K-1
-      prev->used = true;
+      use(prev);
       const double br = p_.blend_ratio * x;
       if (!(prev->act >= br)) return 0;
     }
@@ -242,9 +242,12 @@ Detector::Status Detector::shot_step(MeasureStore& store, int avail, bool finish
   // the structure verdict is formed once the shot has samp_max_frames votes;
   // the rules for 3:2 pulldown shots apply from the frame after the last voter
   if (!cur.has_verdict && p_.samp_max_frames > 0 && cur.voters_seen >= p_.samp_max_frames) {
-    if (cur.analysed.size() < (size_t)p_.samp_max_frames) return kNeedVotes;
-    classify(cur, cur.verdict);
-    cur.has_verdict = true;
+    if (cur.analysed.size() >= (size_t)p_.samp_max_frames) {
+      classify(cur, cur.verdict);
+      cur.has_verdict = true;
+    } else if (!spec_) {
+      return kNeedVotes;
+    }
   }
   if (t_ + 1 >= avail) return kNeedFrames;
   Measure* a = store.find(kFrame, t_, t_ + 1);
@@ -252,7 +255,7 @@ Detector::Status Detector::shot_step(MeasureStore& store, int avail, bool finish
     need.push_back(pair_key(kFrame, t_, t_ + 1));
     return kNeedPairs;
   }
-  a->used = true;
+  use(a);
   const double at = a->act;
   const bool pulldown = cur.has_verdict && cur.verdict.label == ANALYSER_PULLDOWN;
   bool cand = false;
@@ -285,16 +288,21 @@ Detector::Status Detector::shot_step(MeasureStore& store, int avail, bool finish
           if (!a1 || !a2) {
             if (!a1) need.push_back(pair_key(kFrame, t_ + 1, t_ + 2));
             if (!a2) need.push_back(pair_key(kFrame, t_ + 2, t_ + 3));
-            return kNeedPairs;
+            if (!spec_) return kNeedPairs;
+          } else {
+            cand = at < a1->act && a1->act < a2->act;
           }
-          cand = at < a1->act && a1->act < a2->act;
         }
       }
     }
     if (cand) {
       Status st;
-      const int K = pulldown ? deep_check_pulldown(store, t_, T_, finished, avail, need, st)
-                             : deep_check(store, t_, T_, finished, avail, need, st);
+      int K = pulldown ? deep_check_pulldown(store, t_, T_, finished, avail, need, st)
+                       : deep_check(store, t_, T_, finished, avail, need, st);
+      if (st == kNeedPairs && spec_) {
+        K = 0;   // a speculative copy goes on as if there were no boundary at t
+        st = kProgress;
+      }
       if (st != kProgress) return st;
       if (K > 0) {
         cur.last = t_;
@@ -349,10 +357,10 @@ Detector::Status Detector::sampling_step(MeasureStore& store, Shot& sh, std::vec
     Measure* ru = reps ? store.find(kUpperUpper, t, t + 1) : nullptr;
     Measure* rl = reps ? store.find(kLowerLower, t, t + 1) : nullptr;
     if (v0 && v1 && v2 && (!reps || (ru && rl))) {
-      v0->used = v1->used = v2->used = true;
+      use(v0); use(v1); use(v2);
       sh.analysed.push_back({t, v0->amm, v1->amm, v2->amm});
       if (reps) {
-        ru->used = rl->used = true;
+        use(ru); use(rl);
         const double tu = p_.rep_ratio * rl->act, tl = p_.rep_ratio * ru->act;
         sh.reps.push_back(ru->act < tu ? kRepUpper : (rl->act < tl ? kRepLower : kRepNone));
       }
@@ -482,6 +490,23 @@ Detector::Status Detector::run(MeasureStore& store, int avail, bool finished, st
     break;
   }
   if (shot_st == kNeedVotes) shot_st = kNeedPairs;
+  // Prefetch: when the shot detector waits for pairs (a deep check, a ramp
+  // test or the structure verdict), a copy of the detectors runs on over the
+  // frames already available as if the pending test found no boundary, and
+  // asks for the pairs it reads; the next wave computes them beside the
+  // pending ones.  The copy marks nothing as read and is discarded, so the
+  // decisions and the reported measure set are those of the real run.
+  if (!spec_ && shot_st == kNeedPairs && p_.prefetch_frames > 0) {
+    Detector sp = *this;
+    sp.spec_ = true;
+    const int horizon = std::min(avail, t_ + p_.prefetch_frames);
+    for (int guard = 0; guard < 1000000 && sp.t_ < horizon - 1; guard++) {
+      const Status st = sp.shot_step(store, horizon, finished && horizon == avail, need);
+      if (st != kProgress) break;
+    }
+    bool unused = false;
+    for (Shot& sh : sp.open_) sp.sampling_step(store, sh, need, unused);
+  }
   // close shots (in order) whose boundaries and votes are final
   while (!open_.empty()) {
     Shot& sh = open_.front();

@@ -95,7 +95,12 @@ class Detector {
   void classify(const Shot& sh, ShotOut& out) const;
   void finish_clip();
 
+  void use(Measure* m) const {   // a rule read m (a speculative copy reads without reporting)
+    if (!spec_) m->used = true;
+  }
+
   analyser_params p_{};
+  bool spec_ = false;            // a speculative copy that only collects pair requests
   int64_t static_thr_ = 0;
   int t_ = 0;                    // shot detector position (frame under test)
   int T_ = -1;                   // clip length once known

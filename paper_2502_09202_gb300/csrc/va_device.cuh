@@ -61,39 +61,47 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Shared-memory window of one block at a refinement level of block side S
 // (radius 2): WR rows of RW words copied from the 4-byte boundary at or before
 // the window's first byte (candidate dx = -2).  Every block owns one region of
-// kRefineWinWords words that both levels use, so a block's four lanes never
-// touch another block's window and the levels need no CTA barrier; the stride
-// (28 banks) puts the words the level-0 lanes read together on 32 distinct
-// banks (level 1: at most two-way).
+// kRefineWinWords words that both levels use, so a block's lanes never touch
+// another block's window and the levels need no CTA barrier.
 constexpr int kRefineWinWords = 124;
 template <int S>
 struct RefineWin;
 template <>
 struct RefineWin<16> {
-  static constexpr int WR = 20, RW = 6, H = 1;
+  static constexpr int WR = 20, RW = 6;
 };
 template <>
 struct RefineWin<8> {
-  static constexpr int WR = 12, RW = 4, H = 2;
+  static constexpr int WR = 12, RW = 4;
+};
+
+// Lane layout of one block at a refinement level: LPB lanes per block, each
+// with WPL consecutive 4-pixel words of a row and RT rows of the block.
+template <int S, int LPB>
+struct RefineLanes {
+  static constexpr int NQ = S / 4;                       // words per block row
+  static constexpr int WPL = (S == 16 && LPB == 2) ? 2 : 1;
+  static constexpr int CL = NQ / WPL;                    // column lanes
+  static constexpr int H = LPB / CL;                     // row slices
+  static constexpr int RT = S / H;                       // rows per lane
+  static_assert(CL * WPL == NQ && CL * H == LPB, "lane layout");
 };
 
 // Refinement of every block of a tile at one pyramid level (block side S,
 // radius RR), candidates v = 2*parent + d, |d| <= RR (Sec. III.A, coarse to
-// fine block matching).  Four lanes own a block (lanes 4*bl .. 4*bl+3):
+// fine block matching).  LPB lanes own a block (lanes LPB*bl .. LPB*bl+LPB-1):
 //  - they copy the block's window of J into shared memory (cp.async, the
-//    four lanes of a row together; clamp-to-edge loads where the window leaves
-//    the image horizontally, row indices clamped), so a level needs no CTA
-//    barrier;
-//  - lane t covers 4-pixel column t % (S/4) and row slice t / (S/4) of the
-//    block, keeps those I words in registers and slides down the window rows,
-//    feeding all 25 (dx, dy) candidates; the four partial sums are added with
-//    xor shuffles;
+//    lanes of a row together; clamp-to-edge loads where the window leaves the
+//    image horizontally, row indices clamped), so a level needs no CTA barrier;
+//  - a lane covers WPL 4-pixel words of RT rows of the block, keeps those I
+//    words in registers and slides down the window rows, feeding all 25
+//    (dx, dy) candidates; the lanes' partial sums are added with xor shuffles;
 //  - a candidate's key is (cost << 8) + rank with cost = SAD + lambda*|v|_1 and
 //    rank = (|v|_1 - min|v|_1)*25 + dy_i*5 + dx_i, which orders the block's 25
 //    candidates exactly as (cost, |v|_1, vy, vx).
 // Afterwards s_vx/s_vy hold the level-l vectors (visible to the block's own
-// lanes; other threads need a CTA barrier first).  With SUMS the four lanes
-// then add the motion-compensated sums of their pixels (I column in registers,
+// lanes; other threads need a CTA barrier first).  With SUMS the lanes then
+// add the motion-compensated sums of their pixels (I words in registers,
 // warped J from the window) to part[] =
 // {sum I, sum J, sum I^2, sum J^2, sum IJ, sum |I-J|}.
 //
@@ -102,19 +110,22 @@ struct RefineWin<8> {
 // (the caller commits and waits in between), both with the parent passed in
 // (pvx, pvy): a kernel can then issue the first level's copies together with
 // its other loads and wait once.
-template <int S, int RR, int NT, int NB, int TBX, bool SUMS, int PHASE = 0>
+// With IGLOBAL the I words come from the level's plane in global memory
+// (Ig, two words per lane as one 8-byte load) instead of a staged tile s_i.
+template <int S, int RR, int NT, int NB, int TBX, bool SUMS, int PHASE = 0, int LPB = 4, bool IGLOBAL = false>
 __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i, int bx0, int by0, int nbx, int nby,
                                              int lam, int* s_vx, int* s_vy, uint32_t* s_win, uint32_t (&part)[6],
-                                             int tid, int pvx = 0, int pvy = 0) {
+                                             int tid, int pvx = 0, int pvy = 0, const Plane Ig = Plane{}) {
   static_assert(RR == 2, "candidate ranks and window shapes assume radius 2");
   using Wn = RefineWin<S>;
-  constexpr int NQ = S / 4, H = Wn::H, RT = S / H;   // column lanes, row slices, rows per slice
+  using Ln = RefineLanes<S, LPB>;
+  constexpr int NQ = Ln::NQ, WPL = Ln::WPL, CL = Ln::CL, RT = Ln::RT;
   constexpr int IW = TBX * NQ;                       // words per row of the staged I tile
-  static_assert(NQ * H == 4 && Wn::WR % 4 == 0, "four lanes per block");
-  static_assert(NT % 32 == 0 && NT >= NB * 4 && (NB * 4) % 32 == 0, "one task per thread, whole warps");
-  if ((tid & ~31) >= NB * 4) return;   // warps without a block (warp-uniform)
-  const int bl = tid >> 2, t = tid & 3;
-  const int q = t % NQ, h = t / NQ;
+  static_assert(Wn::WR % LPB == 0, "rows split evenly over a block's lanes");
+  static_assert(NT % 32 == 0 && NT >= NB * LPB && (NB * LPB) % 32 == 0, "one task per thread, whole warps");
+  if ((tid & ~31) >= NB * LPB) return;   // warps without a block (warp-uniform)
+  const int bl = tid / LPB, t = tid % LPB;
+  const int q0 = (t % CL) * WPL, h = t / CL;
   const int bxl = bl % TBX, byl = bl / TBX;
   const bool valid = bx0 + bxl < nbx && by0 + byl < nby;
   const int cx = 2 * (PHASE == 0 ? s_vx[bl] : pvx), cy = 2 * (PHASE == 0 ? s_vy[bl] : pvy);
@@ -122,13 +133,13 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
   const int yw = (by0 + byl) * S + cy - RR;
   const int xa = xw & ~3, s8 = 8 * (xw & 3);
   static_assert(Wn::WR * Wn::RW <= kRefineWinWords, "window fits the block's region");
+  static_assert(!IGLOBAL || WPL == 2, "global I words are loaded in pairs");
   uint32_t* const win = s_win + bl * kRefineWinWords;
 
   // ---- staging ----------------------------------------------------------------
-  // The block's four lanes copy each row together (lane t: words t and t + 4):
-  // a warp instruction reads 16 contiguous bytes per block and writes 32
-  // distinct banks.  A window leaving the image horizontally is read
-  // clamp-to-edge, each lane its own rows.
+  // The block's lanes copy each row together (lane t: words t, t + LPB, ...):
+  // a warp instruction reads contiguous bytes per block.  A window leaving the
+  // image horizontally is read clamp-to-edge, each lane its own rows.
   if (PHASE != 2 && valid) {
     const bool inside = xa >= 0 && xa + 4 * Wn::RW <= Jl.w;
     if (inside) {
@@ -136,13 +147,14 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
 #pragma unroll 4
       for (int r = 0; r < Wn::WR; r++) {
         const uint8_t* row = src + (size_t)clampi(yw + r, 0, Jl.h - 1) * Jl.pitch;
-        cp_async4(win + r * Wn::RW + t, row);
-        if (Wn::RW > 4 && t < Wn::RW - 4) cp_async4(win + r * Wn::RW + 4 + t, row + 16);
+#pragma unroll
+        for (int c = 0; c < Wn::RW; c += LPB)
+          if (c + t < Wn::RW) cp_async4(win + r * Wn::RW + c + t, row + 4 * c);
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < Wn::WR / 4; k++) {
-        const int r = t + 4 * k;
+      for (int k = 0; k < Wn::WR / LPB; k++) {
+        const int r = t + LPB * k;
         const uint8_t* row = Jl.p + (size_t)clampi(yw + r, 0, Jl.h - 1) * Jl.pitch;
 #pragma unroll
         for (int c = 0; c < Wn::RW; c++) win[r * Wn::RW + c] = load4_clamped(row, xa + 4 * c, Jl.w);
@@ -150,6 +162,19 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
     }
   }
   if constexpr (PHASE != 1) {   // the rest computes (PHASE 1 only copies)
+    // I words of the lane from global memory, in flight while the window copies land
+    uint32_t gcol[IGLOBAL ? WPL : 1][IGLOBAL ? RT : 1];
+    if constexpr (IGLOBAL) {
+      if (valid) {
+        const uint8_t* ib = Ig.p + (size_t)((by0 + byl) * S + h * RT) * Ig.pitch + (bx0 + bxl) * S + 4 * q0;
+#pragma unroll
+        for (int i = 0; i < RT; i++) {
+          const uint2 v = __ldg(reinterpret_cast<const uint2*>(ib + (size_t)i * Ig.pitch));
+          gcol[0][i] = v.x;
+          gcol[1][i] = v.y;
+        }
+      }
+    }
     if constexpr (PHASE == 0) {
       cp_async_commit();
       cp_async_wait_all();
@@ -163,28 +188,43 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
 #pragma unroll
       for (int d = 0; d < 5; d++) acc[a][d] = 0;
     if (valid) {
-      uint32_t icol[RT];
-      const uint32_t* ip = s_i + (byl * S + h * RT) * IW + bxl * NQ + q;
+      uint32_t icol[WPL][RT];
+      if constexpr (IGLOBAL) {
 #pragma unroll
-      for (int i = 0; i < RT; i++) icol[i] = ip[i * IW];
-      const uint32_t* wp = win + (h * RT) * Wn::RW + q;
+        for (int m = 0; m < WPL; m++)
+#pragma unroll
+          for (int i = 0; i < RT; i++) icol[m][i] = gcol[m][i];
+      } else {
+        const uint32_t* ip = s_i + (byl * S + h * RT) * IW + bxl * NQ + q0;
+#pragma unroll
+        for (int m = 0; m < WPL; m++)
+#pragma unroll
+          for (int i = 0; i < RT; i++) icol[m][i] = ip[i * IW + m];
+      }
+      const uint32_t* wp = win + (h * RT) * Wn::RW + q0;
 #pragma unroll
       for (int w = 0; w < RT + 2 * RR; w++) {
-        const uint32_t w0 = wp[w * Wn::RW], w1 = wp[w * Wn::RW + 1], w2 = wp[w * Wn::RW + 2];
-        const uint32_t u0 = __funnelshift_r(w0, w1, s8), u1 = __funnelshift_r(w1, w2, s8);
-        const uint32_t jw[5] = {u0, __funnelshift_r(u0, u1, 8), __funnelshift_r(u0, u1, 16),
-                                __funnelshift_r(u0, u1, 24), u1};
+        uint32_t wv[WPL + 2], u[WPL + 1];
 #pragma unroll
-        for (int d = 0; d < 5; d++) {
-          const int i = w - d;
-          if (i >= 0 && i < RT) {
+        for (int k = 0; k < WPL + 2; k++) wv[k] = wp[w * Wn::RW + k];
 #pragma unroll
-            for (int a = 0; a < 5; a++) acc[a][d] = sad4(icol[i], jw[a], acc[a][d]);
+        for (int k = 0; k <= WPL; k++) u[k] = __funnelshift_r(wv[k], wv[k + 1], s8);
+#pragma unroll
+        for (int m = 0; m < WPL; m++) {
+          const uint32_t jw[5] = {u[m], __funnelshift_r(u[m], u[m + 1], 8), __funnelshift_r(u[m], u[m + 1], 16),
+                                  __funnelshift_r(u[m], u[m + 1], 24), u[m + 1]};
+#pragma unroll
+          for (int d = 0; d < 5; d++) {
+            const int i = w - d;
+            if (i >= 0 && i < RT) {
+#pragma unroll
+              for (int a = 0; a < 5; a++) acc[a][d] = sad4(icol[m][i], jw[a], acc[a][d]);
+            }
           }
         }
       }
     }
-    // sum the four lanes' partials: every candidate's SAD over the block is below
+    // sum the lanes' partials: every candidate's SAD over the block is below
     // 2^16 (at most 256 pixels * 255), so two candidates share a 32-bit shuffle
     // and their halves never carry into each other
     uint32_t pk[13];
@@ -194,7 +234,7 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
       pk[j] = acc[c0 % 5][c0 / 5] | (c1 < 25 ? acc[c1 % 5][c1 / 5] << 16 : 0u);
     }
 #pragma unroll
-    for (int off = 1; off <= 2; off <<= 1) {
+    for (int off = 1; off < LPB; off <<= 1) {
 #pragma unroll
       for (int j = 0; j < 13; j++) pk[j] += __shfl_xor_sync(0xFFFFFFFFu, pk[j], off);
     }
@@ -229,22 +269,30 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
     }
     if constexpr (SUMS) {
       if (valid) {
-        // pixel (4q + c, i) of the block meets window byte (xw & 3) + 4q + c + dx_i of row i + dy_i
+        // pixel (4(q0+m) + c, i) of the block meets window byte (xw & 3) + 4(q0+m) + c + dx_i
+        // of row i + dy_i
         const int o = (xw & 3) + r % 5, dyi = r / 5, sh = 8 * (o & 3);
-        const uint32_t* ip = s_i + (byl * S + h * RT) * IW + bxl * NQ + q;
-        const uint32_t* jp = win + (h * RT + dyi) * Wn::RW + q + (o >> 2);
         uint32_t si = 0, sj = 0, sii = 0, sjj = 0, sij = 0, sab = 0;
+        const uint32_t* ip = s_i + (byl * S + h * RT) * IW + bxl * NQ + q0;
 #pragma unroll
-        for (int i = 0; i < RT; i++) {
-          const uint32_t iv = ip[i * IW];
-          const uint32_t w0 = jp[i * Wn::RW], w1 = sh ? jp[i * Wn::RW + 1] : 0u;
-          const uint32_t jv = __funnelshift_r(w0, w1, sh);
-          si = __dp4a(iv, 0x01010101u, si);
-          sj = __dp4a(jv, 0x01010101u, sj);
-          sii = __dp4a(iv, iv, sii);
-          sjj = __dp4a(jv, jv, sjj);
-          sij = __dp4a(iv, jv, sij);
-          sab = sad4(iv, jv, sab);
+        for (int m = 0; m < WPL; m++) {
+          const uint32_t* jp = win + (h * RT + dyi) * Wn::RW + q0 + m + (o >> 2);
+#pragma unroll
+          for (int i = 0; i < RT; i++) {
+            // reread (the I words need no registers across the keys): staged tile, or L1
+            const uint32_t iv =
+                IGLOBAL ? __ldg(reinterpret_cast<const uint32_t*>(Ig.p + (size_t)((by0 + byl) * S + h * RT + i) * Ig.pitch +
+                                                                  (bx0 + bxl) * S + 4 * (q0 + m)))
+                        : ip[i * IW + m];
+            const uint32_t w0 = jp[i * Wn::RW], w1 = sh ? jp[i * Wn::RW + 1] : 0u;
+            const uint32_t jv = __funnelshift_r(w0, w1, sh);
+            si = __dp4a(iv, 0x01010101u, si);
+            sj = __dp4a(jv, 0x01010101u, sj);
+            sii = __dp4a(iv, iv, sii);
+            sjj = __dp4a(jv, jv, sjj);
+            sij = __dp4a(iv, jv, sij);
+            sab = sad4(iv, jv, sab);
+          }
         }
         part[0] += si; part[1] += sj; part[2] += sii; part[3] += sjj; part[4] += sij; part[5] += sab;
       }
@@ -273,6 +321,13 @@ __device__ __forceinline__ uint32_t coarse_rows(const uint32_t* wrow, uint32_t i
   // of the block at window row dy, starts at k = 0 and completes at k = 3.
   uint32_t acc[NJ][4];
   uint32_t best[NJ], pend[NJ];   // pend: the previous row's keys, folded in pairs by a 3-input minimum
+#if defined(VA_COARSE_FMIN)
+  // keys + 2^23 are the bit patterns of positive normal floats, which order as
+  // the integers do: the minimum runs as a float minimum
+  float bestf[NJ], pendf[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; j++) bestf[j] = pendf[j] = __uint_as_float(0x7F7FFFFFu);
+#endif
 #pragma unroll
   for (int j = 0; j < NJ; j++) {
     best[j] = 0xFFFFFFFFu;
@@ -301,11 +356,18 @@ __device__ __forceinline__ uint32_t coarse_rows(const uint32_t* wrow, uint32_t i
     if (dy >= 3) {
       const int vy = dy - R - 3;
       const int avy = vy < 0 ? -vy : vy;
+#if defined(VA_COARSE_FMIN)
+      const uint32_t bv = lamM * (uint32_t)avy + ((((uint32_t)avy << 12) | ((uint32_t)(vy + R) << 6)) + 0x00800000u);
+#else
       const uint32_t bv = lamM * (uint32_t)avy + (((uint32_t)avy << 12) | ((uint32_t)(vy + R) << 6));
+#endif
 #pragma unroll
       for (int j = 0; j < NJ; j++) {
         const uint32_t key = acc[j][(dy - 3) & 3] * keyM + bv;
-#if defined(VA_COARSE_NOPEND)
+#if defined(VA_COARSE_FMIN)
+        if (((dy - 3) & 1) == 0 && dy < 2 * R + 3) pendf[j] = __uint_as_float(key);
+        else bestf[j] = fminf(bestf[j], fminf(pendf[j], __uint_as_float(key)));
+#elif defined(VA_COARSE_NOPEND)
         best[j] = min(best[j], key);
 #elif defined(VA_COARSE_MIN2)
         if (((dy - 3) & 1) == 0 && dy < 2 * R + 3) pend[j] = key;
@@ -314,6 +376,60 @@ __device__ __forceinline__ uint32_t coarse_rows(const uint32_t* wrow, uint32_t i
         if (((dy - 3) & 1) == 0 && dy < 2 * R + 3) pend[j] = key;
         else best[j] = __vimin3_u32(best[j], pend[j], key);
 #endif
+      }
+    }
+  }
+#if defined(VA_COARSE_FMIN)
+#pragma unroll
+  for (int j = 0; j < NJ; j++) best[j] = __float_as_uint(bestf[j]) - 0x00800000u;
+#endif
+  uint32_t tbest = 0xFFFFFFFFu;
+#pragma unroll
+  for (int j = 0; j < NJ; j++) {
+    const int vx = vx0 + j;
+    const int avx = vx < 0 ? -vx : vx;
+    const uint32_t a = lamM * (uint32_t)avx + ((uint32_t)avx << 12) + (uint32_t)(vx + R);
+    tbest = min(tbest, best[j] + a);
+  }
+  return tbest;
+}
+
+// The rows of coarse_rows for NJ consecutive vx candidates whose window words
+// are read through one pointer each (base[j] points at the candidate's first
+// row in the byte-shifted copy of its alignment).
+template <int R, int NJ, int WWORDS>
+__device__ __forceinline__ uint32_t coarse_rows_ptr(const uint32_t* const (&base)[NJ], uint32_t i0, uint32_t i1,
+                                                    uint32_t i2, uint32_t i3, int vx0, uint32_t lamM, uint32_t keyM) {
+  uint32_t acc[NJ][4];
+  uint32_t best[NJ], pend[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; j++) {
+    best[j] = 0xFFFFFFFFu;
+    pend[j] = 0xFFFFFFFFu;
+#pragma unroll
+    for (int k = 0; k < 4; k++) acc[j][k] = 0;
+  }
+#pragma unroll
+  for (int dy = 0; dy < 2 * R + 4; dy++) {
+    uint32_t w[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; j++) w[j] = base[j][dy * WWORDS];
+#pragma unroll
+    for (int j = 0; j < NJ; j++) {
+      if (dy <= 2 * R) acc[j][dy & 3] = sad4(i0, w[j], 0u);
+      if (dy >= 1 && dy - 1 <= 2 * R) acc[j][(dy - 1) & 3] = sad4(i1, w[j], acc[j][(dy - 1) & 3]);
+      if (dy >= 2 && dy - 2 <= 2 * R) acc[j][(dy - 2) & 3] = sad4(i2, w[j], acc[j][(dy - 2) & 3]);
+      if (dy >= 3) acc[j][(dy - 3) & 3] = sad4(i3, w[j], acc[j][(dy - 3) & 3]);
+    }
+    if (dy >= 3) {
+      const int vy = dy - R - 3;
+      const int avy = vy < 0 ? -vy : vy;
+      const uint32_t bv = lamM * (uint32_t)avy + (((uint32_t)avy << 12) | ((uint32_t)(vy + R) << 6));
+#pragma unroll
+      for (int j = 0; j < NJ; j++) {
+        const uint32_t key = acc[j][(dy - 3) & 3] * keyM + bv;
+        if (((dy - 3) & 1) == 0 && dy < 2 * R + 3) pend[j] = key;
+        else best[j] = __vimin3_u32(best[j], pend[j], key);
       }
     }
   }
@@ -326,6 +442,44 @@ __device__ __forceinline__ uint32_t coarse_rows(const uint32_t* wrow, uint32_t i
     tbest = min(tbest, best[j] + a);
   }
   return tbest;
+}
+
+// The coarse search with radius 16 as 11 groups of 3 consecutive vx per block
+// (vx = -16 + 3g .. -14 + 3g): every thread has the same work, so no warp waits
+// at the tile's barrier for a lighter one.  Window layout as in coarse_rows with
+// the four byte-shifted copies.
+template <int TBX, int TBY, int NT>
+__device__ __forceinline__ void coarse_phase_g3(const uint32_t* jwin, const uint32_t* iwin, int bx0, int by0, int nbx,
+                                                int nby, int lam, uint32_t keyM, uint32_t* s_best32, int* s_vx,
+                                                int* s_vy, int tid) {
+  constexpr int R = 16, NGRP = 11, NB = TBX * TBY, WWORDS = TBX + 9;
+  constexpr int COPY = (TBY * 4 + 2 * R) * WWORDS;
+  static_assert(NT >= NB * NGRP, "coarse thread layout");
+  const bool busy = tid < NB * NGRP;
+  const int bl = busy ? tid / NGRP : 0, g = busy ? tid % NGRP : 0;
+  const int bxl = bl % TBX, byl = bl / TBX;
+  const bool active = busy && (bx0 + bxl < nbx) && (by0 + byl < nby);
+  const uint32_t i0 = iwin[(byl * 4 + 0) * TBX + bxl], i1 = iwin[(byl * 4 + 1) * TBX + bxl];
+  const uint32_t i2 = iwin[(byl * 4 + 2) * TBX + bxl], i3 = iwin[(byl * 4 + 3) * TBX + bxl];
+  const uint32_t lamM = (uint32_t)lam * keyM;
+  const uint32_t* row0 = jwin + (byl * 4) * WWORDS + bxl;
+  const uint32_t* base[3];
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    const int o = 3 * g + j;   // vx + R: byte offset of the candidate in the window row
+    base[j] = row0 + (o & 3) * COPY + (o >> 2);
+  }
+  uint32_t tbest = 0xFFFFFFFFu;
+  if (tid < (NB * NGRP + 31) / 32 * 32)
+    tbest = coarse_rows_ptr<R, 3, WWORDS>(base, i0, i1, i2, i3, -R + 3 * g, lamM, keyM);
+  if (active) atomicMin(&s_best32[bl], tbest);
+  __syncthreads();
+  for (int i = tid; i < NB; i += NT) {
+    const uint32_t tb = s_best32[i] % kCoarseKeyM;
+    s_vx[i] = (int)(tb & 63u) - R;
+    s_vy[i] = (int)((tb >> 6) & 63u) - R;
+  }
+  __syncthreads();
 }
 
 // Exhaustive search of every block of a tile on the coarsest level (block

@@ -108,6 +108,10 @@ int validate_params(const analyser_params& p, std::string& why) {
     return ANALYSER_ERR_INVALID_ARG;
   }
   if (p.rep_probe < 0 || p.rep_probe > 100000) { why = "rep_probe out of range"; return ANALYSER_ERR_INVALID_ARG; }
+  if (p.prefetch_frames < 0 || p.prefetch_frames > 1000000) {
+    why = "prefetch_frames out of range";
+    return ANALYSER_ERR_INVALID_ARG;
+  }
   if (!(p.fast_lambda >= 0) || !(p.fast_rise >= 0) || !(p.fast_tau >= 0) || !(p.deep_rho >= 0) || !(p.deep_tau >= 0) ||
       !(p.done_eps >= 0) || !(p.steady_gamma >= 0) || !(p.lag_rho >= 0) || !(p.blend_ratio >= 0) ||
       !(p.pd_rho >= 0) || !(p.pd_gamma_new >= 0) || !(p.pd_gamma_old >= 0) || !(p.rep_ratio >= 0) ||

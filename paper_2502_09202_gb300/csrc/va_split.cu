@@ -12,8 +12,11 @@
 #ifndef VA_COARSE_MINB
 #define VA_COARSE_MINB 7
 #endif
-#ifndef VA_REFINE_MINB
-#define VA_REFINE_MINB 8
+#ifndef VA_REFINE_LPB
+#define VA_REFINE_LPB 4      // lanes per block in the refinement kernel (2 or 4)
+#endif
+#ifndef VA_REFINE_REGS
+#define VA_REFINE_REGS (VA_REFINE_LPB == 2 ? 80 : 64)   // register budget per thread
 #endif
 
 namespace va {
@@ -23,7 +26,12 @@ template <int R, int TBX, int TBY>
 struct CoarseShape {
   static constexpr int G = (2 * R + 4) / 4;
   static constexpr int NB = TBX * TBY;
-  static constexpr int NT = (NB * G + 31) / 32 * 32;
+#if defined(VA_COARSE_G4)
+  static constexpr bool G3 = false;
+#else
+  static constexpr bool G3 = R == 16;   // radius 16: 11 equal groups of 3 vx per block
+#endif
+  static constexpr int NT = G3 ? (NB * 11 + 31) / 32 * 32 : (NB * G + 31) / 32 * 32;
   static constexpr int WROWS = TBY * kCoarseSide + 2 * R;
   static constexpr int WWORDS = TBX + G;
   static constexpr int MINB = VA_COARSE_MINB * 288 / NT > 0 ? VA_COARSE_MINB * 288 / NT : 1;  // resident CTAs per SM
@@ -32,8 +40,10 @@ struct CoarseShape {
 template <int TBX, int TBY>
 struct RefineShape {
   static constexpr int NB = TBX * TBY;
-  static constexpr int NT = NB * 4 < 64 ? 64 : NB * 4;   // one level-0 task (block, column) per thread
-  static constexpr int MINB = VA_REFINE_MINB * 128 / NT;  // resident CTAs per SM the register budget allows
+  static constexpr int LPB = VA_REFINE_LPB;
+  static constexpr int NT = NB * LPB < 32 ? 32 : NB * LPB;   // LPB lanes per block
+  static constexpr int MINB0 = 65536 / (VA_REFINE_REGS * NT);
+  static constexpr int MINB = MINB0 < 1 ? 1 : (MINB0 > 32 ? 32 : MINB0);   // resident CTAs per SM at the budget
 };
 
 // Copies the job holding `item` to shared memory: thread t checks jobs t,
@@ -97,8 +107,12 @@ __global__ void __launch_bounds__(CoarseShape<R, TBX, TBY>::NT, CoarseShape<R, T
   }
   for (int i = tid; i < NB; i += NT) s_best32[i] = 0xFFFFFFFFu;
   __syncthreads();
-  coarse_phase<R, TBX, TBY, NT, true>(s_jwin, s_iw, bx0, by0, nbx, nby, b.cfg.lambda, b.cfg.key_mul, s_best32, s_vx,
-                                       s_vy, tid);
+  if constexpr (S::G3)
+    coarse_phase_g3<TBX, TBY, NT>(s_jwin, s_iw, bx0, by0, nbx, nby, b.cfg.lambda, b.cfg.key_mul, s_best32, s_vx,
+                                  s_vy, tid);
+  else
+    coarse_phase<R, TBX, TBY, NT, true>(s_jwin, s_iw, bx0, by0, nbx, nby, b.cfg.lambda, b.cfg.key_mul, s_best32,
+                                         s_vx, s_vy, tid);
   for (int i = tid; i < NB; i += NT) {
     const int bx = bx0 + i % TBX, by = by0 + i / TBX;
     if (bx < nbx && by < nby) jb.cvec[(size_t)by * nbx + bx] = make_short2((short)s_vx[i], (short)s_vy[i]);
@@ -108,8 +122,9 @@ __global__ void __launch_bounds__(CoarseShape<R, TBX, TBY>::NT, CoarseShape<R, T
 template <int TBX, int TBY>
 __global__ void __launch_bounds__(RefineShape<TBX, TBY>::NT, RefineShape<TBX, TBY>::MINB) refine_kernel(const PairBatch b) {
   using S = RefineShape<TBX, TBY>;
-  constexpr int NB = S::NB, NT = S::NT;
-  __shared__ __align__(16) uint32_t s_i0[TBY * 16 * TBX * 4];
+  constexpr int NB = S::NB, NT = S::NT, LPB = S::LPB;
+  constexpr bool IG = LPB == 2;   // two lanes per block read their level-0 I words from global memory
+  __shared__ __align__(16) uint32_t s_i0[IG ? 4 : TBY * 16 * TBX * 4];
   __shared__ __align__(16) uint32_t s_i1[TBY * 8 * TBX * 2];
   __shared__ uint32_t s_win[NB * kRefineWinWords];
   __shared__ int s_vx[NB], s_vy[NB];
@@ -122,10 +137,12 @@ __global__ void __launch_bounds__(RefineShape<TBX, TBY>::NT, RefineShape<TBX, TB
   const int local = item - jb.item_begin;
   const int bx0 = (local % jb.tiles_x) * TBX, by0 = (local / jb.tiles_x) * TBY;
   const int nbx = jb.nbx, nby = jb.nby;
-  for (int c = tid; c < TBY * 16 * TBX; c += NT) {
-    const int r = c / TBX, k = c - r * TBX;
-    if (bx0 + k < nbx && by0 + r / 16 < nby)
-      cp_async16(&s_i0[c * 4], jb.I[0].p + (size_t)(by0 * 16 + r) * jb.I[0].pitch + (bx0 + k) * 16);
+  if constexpr (!IG) {
+    for (int c = tid; c < TBY * 16 * TBX; c += NT) {
+      const int r = c / TBX, k = c - r * TBX;
+      if (bx0 + k < nbx && by0 + r / 16 < nby)
+        cp_async16(&s_i0[c * 4], jb.I[0].p + (size_t)(by0 * 16 + r) * jb.I[0].pitch + (bx0 + k) * 16);
+    }
   }
   for (int c = tid; c < TBY * 8 * TBX; c += NT) {
     const int r = c / TBX, k = c - r * TBX;
@@ -138,17 +155,18 @@ __global__ void __launch_bounds__(RefineShape<TBX, TBY>::NT, RefineShape<TBX, TB
   uint32_t part[6] = {0, 0, 0, 0, 0, 0};
   short2 pv = make_short2(0, 0);
   {
-    const int bl = tid >> 2, bx = bx0 + bl % TBX, by = by0 + bl / TBX;
+    const int bl = tid / LPB, bx = bx0 + bl % TBX, by = by0 + bl / TBX;
     if (bl < NB && bx < nbx && by < nby) pv = jb.cvec[(size_t)by * nbx + bx];
   }
-  refine_level<8, 2, NT, NB, TBX, false, 1>(jb.J[1], s_i1, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part, tid,
-                                            pv.x, pv.y);
+  refine_level<8, 2, NT, NB, TBX, false, 1, LPB>(jb.J[1], s_i1, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part,
+                                                 tid, pv.x, pv.y);
   cp_async_commit();
   cp_async_wait_all();
   __syncthreads();
-  refine_level<8, 2, NT, NB, TBX, false, 2>(jb.J[1], s_i1, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part, tid,
-                                            pv.x, pv.y);
-  refine_level<16, 2, NT, NB, TBX, true>(jb.J[0], s_i0, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part, tid);
+  refine_level<8, 2, NT, NB, TBX, false, 2, LPB>(jb.J[1], s_i1, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part,
+                                                 tid, pv.x, pv.y);
+  refine_level<16, 2, NT, NB, TBX, true, 0, LPB, IG>(jb.J[0], s_i0, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part,
+                                                     tid, 0, 0, jb.I[0]);
   __syncthreads();   // every block's vector is read below
   sums_phase<TBX, TBY, NT>(b, jb, bx0, by0, 16, true, part, s_vx, s_vy, s_red, tid);
 }

@@ -37,7 +37,7 @@ class Params(ctypes.Structure):
         ("device", c_int), ("window_frames", c_int), ("mem_budget_bytes", c_ull), ("want_motion", c_int),
         ("tile_x", c_int), ("tile_y", c_int), ("time_kernels", c_int),
         ("step_frames", c_int), ("kernel_mode", c_int), ("want_histogram", c_int),
-        ("wait_timeout_ms", c_double),
+        ("prefetch_frames", c_int), ("wait_timeout_ms", c_double),
     ]
 
 

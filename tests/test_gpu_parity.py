@@ -348,3 +348,22 @@ def test_every_accepted_search_parameter_matches_the_oracle(levels, radius, refi
         ref, vec = _oracle_pair(kinds[k], frames[ia[k]], frames[ib[k]], sp)
         assert list(rec[k]) == [ref[f] for f in REC7], (k, kinds[k])
         assert np.array_equal(mot[k], vec), (k, kinds[k])
+
+
+def test_served_requests_match_the_oracle():
+    """Requests drawn as in the served workload (Poisson arrivals, mixed
+    structures, lengths 30-300, here at the two smallest sizes), submitted while
+    others run and admitted under a budget that holds only some at a time: every
+    result equals the oracle's analysis of the same clip, value by value."""
+    api = _api()
+    reqs = synth.config_served(nrequests=5, length_range=(30, 120), resolutions=((320, 180), (640, 360)))
+    clips = [synth.Clip(s).frames() for _, s in reqs]
+    srv = api.Server(budget_bytes=48 << 20)      # one 640x360 window (36 MB) at a time
+    tickets = []
+    for (_, s), f in zip(reqs, clips):
+        tickets.append(srv.submit(f, s.fps))
+        srv.step()
+    srv.drain()
+    for t, f in zip(tickets, clips):
+        _compare_results(srv.poll(t), OA.analyse_frames(f))
+    srv.close()
