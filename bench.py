@@ -314,7 +314,7 @@ def run_configs(args):
         T, H, W = host.shape
 
         def step():
-            a = api.Analyser(W, H, spec.fps, window_frames=args.window)
+            a = api.Analyser(W, H, spec.fps, window_frames=args.window, **args.overrides)
             a.push_device(dev)
             a.finish()
             r = a.results()
@@ -335,7 +335,7 @@ def run_configs(args):
                     "cuts": r["cuts"], "truth_cuts": truth["cuts"], "dissolves": r["dissolves"],
                     "truth_dissolves": truth["dissolves"], "label": r["label"], "truth_structure": truth["structure"],
                     "pulldown_phase": r["pulldown_phase"], "truth_phase": truth["pulldown_phase"]})
-    print(json.dumps({"mode": "configs", "results": out}))
+    print(json.dumps({"mode": "configs", "param_overrides": args.overrides, "results": out}))
     return 0
 
 
@@ -355,7 +355,7 @@ def run_batched(args):
     def plain_pass():
         out, launches = [], 0
         for s, f in zip(specs, clips):
-            with api.Analyser(s.width, s.height, s.fps) as a:
+            with api.Analyser(s.width, s.height, s.fps, **args.overrides) as a:
                 a.push(f)
                 a.finish()
                 out.append(a.results())
@@ -363,7 +363,7 @@ def run_batched(args):
         return out, launches
 
     def batched_pass():
-        srv = api.Server(budget_bytes=int(args.budget_gb * (1 << 30)))
+        srv = api.Server(budget_bytes=int(args.budget_gb * (1 << 30)), **args.overrides)
         tickets = [srv.submit(f, s.fps) for s, f in zip(specs, clips)]
         srv.drain()
         out = [srv.poll(t) for t in tickets]
@@ -425,12 +425,12 @@ def run_served(args):
     _warm_tiles(api, [(s.width, s.height) for _, s in reqs])
     # a running service is warm: one untimed pass of the same requests, all at
     # once, fills the memory cache for every clip size before the arrivals start
-    warm = api.Server(budget_bytes=int(args.budget_gb * (1 << 30)))
+    warm = api.Server(budget_bytes=int(args.budget_gb * (1 << 30)), **args.overrides)
     for i, (_, s) in enumerate(reqs):
         warm.submit(clips[i], s.fps)
     warm.drain()
     warm.close()
-    srv = api.Server(budget_bytes=int(args.budget_gb * (1 << 30)))
+    srv = api.Server(budget_bytes=int(args.budget_gb * (1 << 30)), **args.overrides)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     pending = list(range(len(reqs)))
@@ -452,7 +452,7 @@ def run_served(args):
     same = True
     for i in check:
         s = reqs[i][1]
-        with api.Analyser(s.width, s.height, s.fps) as a:
+        with api.Analyser(s.width, s.height, s.fps, **args.overrides) as a:
             a.push(clips[i])
             a.finish()
             same = same and _same_decisions(a.results(), srv.poll(tickets[i]))
@@ -492,7 +492,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
 
     def one_step_device(time_kernels=0):
-        a = api.Analyser(W, H, spec.fps, device=local, time_kernels=time_kernels, window_frames=args.window)
+        a = api.Analyser(W, H, spec.fps, device=local, time_kernels=time_kernels, window_frames=args.window,
+                         **args.overrides)
         a.push_device(dev)
         a.finish()
         res = a.results()
@@ -501,7 +502,7 @@ def run_gpu(args):
         return res, prof
 
     def one_step_host():
-        a = api.Analyser(W, H, spec.fps, device=local, window_frames=args.window)
+        a = api.Analyser(W, H, spec.fps, device=local, window_frames=args.window, **args.overrides)
         a.push_host_ptr(pinned.data_ptr(), W, T)
         a.finish()
         res = a.results()
@@ -572,7 +573,8 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "frames": T, "width": W, "height": H, "fps": spec.fps,
                    "parallelism": f"replicas{world}", "l2": "inputs (3.1 GB per step) larger than L2",
                    "window_frames": args.window, "pairs_per_step": profs[-1]["pairs"], "waves_per_step": profs[-1]["waves"],
-                   "cuts": res["cuts"], "dissolves": res["dissolves"], "label": res["label"]},
+                   "cuts": res["cuts"], "dissolves": res["dissolves"], "label": res["label"],
+                   "param_overrides": args.overrides},
         "e2e": {"value": e2e_value, "unit": "frames/s", "ms_per_step": ms_e2e,
                 "h2d_bytes_per_step": int(hprofs[-1]["h2d_bytes"]), "d2h_bytes_per_step": int(hprofs[-1]["d2h_bytes"]),
                 "h2d_link_gbs": link_gbs},
@@ -601,6 +603,19 @@ def run_gpu(args):
     return 0
 
 
+def _overrides(items):
+    """NAME=VALUE analyser parameter overrides, typed by the parameter block's fields."""
+    from paper_2502_09202_gb300 import native as N
+    types = {name: t for name, t in N.Params._fields_}
+    out = {}
+    for it in items:
+        name, _, val = it.partition("=")
+        if name not in types:
+            raise SystemExit(f"unknown analyser parameter {name!r}")
+        out[name] = float(val) if types[name].__name__ in ("c_double", "c_float") else int(val)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -617,7 +632,10 @@ def main():
     ap.add_argument("--length-scale", type=float, default=1.0)
     ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--pairs", type=int, default=64)
+    ap.add_argument("--set", action="append", default=[], metavar="NAME=VALUE",
+                    help="analyser parameter override (repeatable), e.g. --set prefetch_frames=64")
     args = ap.parse_args()
+    args.overrides = _overrides(args.set)
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "kernel":

@@ -394,94 +394,6 @@ __device__ __forceinline__ uint32_t coarse_rows(const uint32_t* wrow, uint32_t i
   return tbest;
 }
 
-// The rows of coarse_rows for NJ consecutive vx candidates whose window words
-// are read through one pointer each (base[j] points at the candidate's first
-// row in the byte-shifted copy of its alignment).
-template <int R, int NJ, int WWORDS>
-__device__ __forceinline__ uint32_t coarse_rows_ptr(const uint32_t* const (&base)[NJ], uint32_t i0, uint32_t i1,
-                                                    uint32_t i2, uint32_t i3, int vx0, uint32_t lamM, uint32_t keyM) {
-  uint32_t acc[NJ][4];
-  uint32_t best[NJ], pend[NJ];
-#pragma unroll
-  for (int j = 0; j < NJ; j++) {
-    best[j] = 0xFFFFFFFFu;
-    pend[j] = 0xFFFFFFFFu;
-#pragma unroll
-    for (int k = 0; k < 4; k++) acc[j][k] = 0;
-  }
-#pragma unroll
-  for (int dy = 0; dy < 2 * R + 4; dy++) {
-    uint32_t w[NJ];
-#pragma unroll
-    for (int j = 0; j < NJ; j++) w[j] = base[j][dy * WWORDS];
-#pragma unroll
-    for (int j = 0; j < NJ; j++) {
-      if (dy <= 2 * R) acc[j][dy & 3] = sad4(i0, w[j], 0u);
-      if (dy >= 1 && dy - 1 <= 2 * R) acc[j][(dy - 1) & 3] = sad4(i1, w[j], acc[j][(dy - 1) & 3]);
-      if (dy >= 2 && dy - 2 <= 2 * R) acc[j][(dy - 2) & 3] = sad4(i2, w[j], acc[j][(dy - 2) & 3]);
-      if (dy >= 3) acc[j][(dy - 3) & 3] = sad4(i3, w[j], acc[j][(dy - 3) & 3]);
-    }
-    if (dy >= 3) {
-      const int vy = dy - R - 3;
-      const int avy = vy < 0 ? -vy : vy;
-      const uint32_t bv = lamM * (uint32_t)avy + (((uint32_t)avy << 12) | ((uint32_t)(vy + R) << 6));
-#pragma unroll
-      for (int j = 0; j < NJ; j++) {
-        const uint32_t key = acc[j][(dy - 3) & 3] * keyM + bv;
-        if (((dy - 3) & 1) == 0 && dy < 2 * R + 3) pend[j] = key;
-        else best[j] = __vimin3_u32(best[j], pend[j], key);
-      }
-    }
-  }
-  uint32_t tbest = 0xFFFFFFFFu;
-#pragma unroll
-  for (int j = 0; j < NJ; j++) {
-    const int vx = vx0 + j;
-    const int avx = vx < 0 ? -vx : vx;
-    const uint32_t a = lamM * (uint32_t)avx + ((uint32_t)avx << 12) + (uint32_t)(vx + R);
-    tbest = min(tbest, best[j] + a);
-  }
-  return tbest;
-}
-
-// The coarse search with radius 16 as 11 groups of 3 consecutive vx per block
-// (vx = -16 + 3g .. -14 + 3g): every thread has the same work, so no warp waits
-// at the tile's barrier for a lighter one.  Window layout as in coarse_rows with
-// the four byte-shifted copies.
-template <int TBX, int TBY, int NT>
-__device__ __forceinline__ void coarse_phase_g3(const uint32_t* jwin, const uint32_t* iwin, int bx0, int by0, int nbx,
-                                                int nby, int lam, uint32_t keyM, uint32_t* s_best32, int* s_vx,
-                                                int* s_vy, int tid) {
-  constexpr int R = 16, NGRP = 11, NB = TBX * TBY, WWORDS = TBX + 9;
-  constexpr int COPY = (TBY * 4 + 2 * R) * WWORDS;
-  static_assert(NT >= NB * NGRP, "coarse thread layout");
-  const bool busy = tid < NB * NGRP;
-  const int bl = busy ? tid / NGRP : 0, g = busy ? tid % NGRP : 0;
-  const int bxl = bl % TBX, byl = bl / TBX;
-  const bool active = busy && (bx0 + bxl < nbx) && (by0 + byl < nby);
-  const uint32_t i0 = iwin[(byl * 4 + 0) * TBX + bxl], i1 = iwin[(byl * 4 + 1) * TBX + bxl];
-  const uint32_t i2 = iwin[(byl * 4 + 2) * TBX + bxl], i3 = iwin[(byl * 4 + 3) * TBX + bxl];
-  const uint32_t lamM = (uint32_t)lam * keyM;
-  const uint32_t* row0 = jwin + (byl * 4) * WWORDS + bxl;
-  const uint32_t* base[3];
-#pragma unroll
-  for (int j = 0; j < 3; j++) {
-    const int o = 3 * g + j;   // vx + R: byte offset of the candidate in the window row
-    base[j] = row0 + (o & 3) * COPY + (o >> 2);
-  }
-  uint32_t tbest = 0xFFFFFFFFu;
-  if (tid < (NB * NGRP + 31) / 32 * 32)
-    tbest = coarse_rows_ptr<R, 3, WWORDS>(base, i0, i1, i2, i3, -R + 3 * g, lamM, keyM);
-  if (active) atomicMin(&s_best32[bl], tbest);
-  __syncthreads();
-  for (int i = tid; i < NB; i += NT) {
-    const uint32_t tb = s_best32[i] % kCoarseKeyM;
-    s_vx[i] = (int)(tb & 63u) - R;
-    s_vy[i] = (int)((tb >> 6) & 63u) - R;
-  }
-  __syncthreads();
-}
-
 // Exhaustive search of every block of a tile on the coarsest level (block
 // side 4, radius R): threads [0, NB*R/2) own one block and 4 consecutive vx
 // candidates each (vx = -R .. R-1), threads [NB*R/2, NB*R/2 + NB) one block

@@ -26,12 +26,7 @@ template <int R, int TBX, int TBY>
 struct CoarseShape {
   static constexpr int G = (2 * R + 4) / 4;
   static constexpr int NB = TBX * TBY;
-#if defined(VA_COARSE_G4)
-  static constexpr bool G3 = false;
-#else
-  static constexpr bool G3 = R == 16;   // radius 16: 11 equal groups of 3 vx per block
-#endif
-  static constexpr int NT = G3 ? (NB * 11 + 31) / 32 * 32 : (NB * G + 31) / 32 * 32;
+  static constexpr int NT = (NB * G + 31) / 32 * 32;
   static constexpr int WROWS = TBY * kCoarseSide + 2 * R;
   static constexpr int WWORDS = TBX + G;
   static constexpr int MINB = VA_COARSE_MINB * 288 / NT > 0 ? VA_COARSE_MINB * 288 / NT : 1;  // resident CTAs per SM
@@ -107,12 +102,8 @@ __global__ void __launch_bounds__(CoarseShape<R, TBX, TBY>::NT, CoarseShape<R, T
   }
   for (int i = tid; i < NB; i += NT) s_best32[i] = 0xFFFFFFFFu;
   __syncthreads();
-  if constexpr (S::G3)
-    coarse_phase_g3<TBX, TBY, NT>(s_jwin, s_iw, bx0, by0, nbx, nby, b.cfg.lambda, b.cfg.key_mul, s_best32, s_vx,
-                                  s_vy, tid);
-  else
-    coarse_phase<R, TBX, TBY, NT, true>(s_jwin, s_iw, bx0, by0, nbx, nby, b.cfg.lambda, b.cfg.key_mul, s_best32,
-                                         s_vx, s_vy, tid);
+  coarse_phase<R, TBX, TBY, NT, true>(s_jwin, s_iw, bx0, by0, nbx, nby, b.cfg.lambda, b.cfg.key_mul, s_best32, s_vx,
+                                       s_vy, tid);
   for (int i = tid; i < NB; i += NT) {
     const int bx = bx0 + i % TBX, by = by0 + i / TBX;
     if (bx < nbx && by < nby) jb.cvec[(size_t)by * nbx + bx] = make_short2((short)s_vx[i], (short)s_vy[i]);
