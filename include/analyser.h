@@ -121,7 +121,7 @@ typedef struct {
   int want_histogram;                  /* per-frame luma histogram and its statistics (0) */
   int prefetch_frames;                 /* when the detectors wait for pairs, a look-ahead over at most
                                           this many frames asks for the pairs they will read next
-                                          (computed in the same wave; decisions unchanged) (0) */
+                                          (computed in the same wave; decisions unchanged) (256) */
   double wait_timeout_ms;              /* host watchdog: a wave or frame copy not complete after this
                                           many ms fails the call with ANALYSER_ERR_TIMEOUT (sticky);
                                           0 = wait without a limit (0) */

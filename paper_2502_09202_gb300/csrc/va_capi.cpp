@@ -129,7 +129,7 @@ int analyser_default_params(analyser_params* p) {
   p->step_frames = 32;
   p->kernel_mode = 0;
   p->want_histogram = 0;
-  p->prefetch_frames = 0;
+  p->prefetch_frames = 256;
   p->wait_timeout_ms = 0.0;
   return ANALYSER_OK;
 }

@@ -242,12 +242,9 @@ Detector::Status Detector::shot_step(MeasureStore& store, int avail, bool finish
   // the structure verdict is formed once the shot has samp_max_frames votes;
   // the rules for 3:2 pulldown shots apply from the frame after the last voter
   if (!cur.has_verdict && p_.samp_max_frames > 0 && cur.voters_seen >= p_.samp_max_frames) {
-    if (cur.analysed.size() >= (size_t)p_.samp_max_frames) {
-      classify(cur, cur.verdict);
-      cur.has_verdict = true;
-    } else if (!spec_) {
-      return kNeedVotes;
-    }
+    if (cur.analysed.size() < (size_t)p_.samp_max_frames) return kNeedVotes;
+    classify(cur, cur.verdict);
+    cur.has_verdict = true;
   }
   if (t_ + 1 >= avail) return kNeedFrames;
   Measure* a = store.find(kFrame, t_, t_ + 1);
@@ -259,7 +256,10 @@ Detector::Status Detector::shot_step(MeasureStore& store, int avail, bool finish
   const double at = a->act;
   const bool pulldown = cur.has_verdict && cur.verdict.label == ANALYSER_PULLDOWN;
   bool cand = false;
-  if ((int)hist_.size() >= p_.jback) {
+  // a speculative copy that passed over a pending deep check tests no frame
+  // that a boundary found there would take
+  const bool quiet = spec_ && t_ <= spec_quiet_;
+  if ((int)hist_.size() >= p_.jback && !quiet) {
     if (pulldown) {
       const int pos = ((t_ - cur.verdict.phase) % 5 + 5) % 5;
       if ((pos == 4 || pos == 0) && t_ - 5 >= cur.first) {
@@ -302,6 +302,7 @@ Detector::Status Detector::shot_step(MeasureStore& store, int avail, bool finish
       if (st == kNeedPairs && spec_) {
         K = 0;   // a speculative copy goes on as if there were no boundary at t
         st = kProgress;
+        spec_quiet_ = t_ + p_.kmax;
       }
       if (st != kProgress) return st;
       if (K > 0) {

@@ -101,6 +101,7 @@ class Detector {
 
   analyser_params p_{};
   bool spec_ = false;            // a speculative copy that only collects pair requests
+  int spec_quiet_ = -1;          // (speculative copy) last frame a pending deep check could take
   int64_t static_thr_ = 0;
   int t_ = 0;                    // shot detector position (frame under test)
   int T_ = -1;                   // clip length once known

@@ -27,24 +27,34 @@ def _chunk(args):
     return synth.Clip(spec).frames(s, e)
 
 
+_FRAMES = {}
+
+
 def _frames(spec):
+    if spec.name in _FRAMES:
+        return _FRAMES[spec.name]
+    _FRAMES.clear()
     out = np.empty((spec.nframes, spec.height, spec.width), np.uint8)
     jobs = [(spec, s, min(s + 50, spec.nframes)) for s in range(0, spec.nframes, 50)]
     with ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 4), mp_context=mp.get_context("spawn")) as ex:
         for (_, s, e), arr in zip(jobs, ex.map(_chunk, jobs)):
             out[s:e] = arr
+    _FRAMES[spec.name] = out
     return out
 
 
 @pytest.mark.parametrize("name", sorted(SPECS))
-def test_full_size_workload_equals_the_stored_oracle_run(name):
+@pytest.mark.parametrize("prefetch", [0, 256])
+def test_full_size_workload_equals_the_stored_oracle_run(name, prefetch):
+    """prefetch > 0: the speculative pair requests change the waves, not one
+    decision or reported value."""
     from paper_2502_09202_gb300 import api
     with gzip.open(os.path.join(GOLDEN, f"oracle_{name}.json.gz"), "rt") as f:
         ref = json.load(f)
     spec = SPECS[name]()
     frames = _frames(spec)
     dev = torch.from_numpy(frames).cuda()
-    with api.Analyser(spec.width, spec.height, spec.fps, window_frames=512) as a:
+    with api.Analyser(spec.width, spec.height, spec.fps, window_frames=512, prefetch_frames=prefetch) as a:
         a.push_device(dev)
         a.finish()
         got = a.results()

@@ -108,7 +108,7 @@ def test_offline_handle_refuses_frames(native):
     native.lib.analyser_destroy(h)
 
 
-def _offline(frames, params=OA.Params()):
+def _offline(frames, params=OA.Params(), **overrides):
     from paper_2502_09202_gb300 import api
     o = OA.OracleAnalyser(lambda t: frames[t], len(frames), params)
     ref = o.run()
@@ -117,7 +117,7 @@ def _offline(frames, params=OA.Params()):
         m = o.m(kind, a, b)
         return [m[k] for k in OM.REC_FIELDS]
 
-    got = api.detect_offline(frames.shape[2], frames.shape[1], len(frames), get)
+    got = api.detect_offline(frames.shape[2], frames.shape[1], len(frames), get, **overrides)
     return got, ref
 
 
@@ -141,8 +141,11 @@ def test_library_detectors_equal_oracle_on_small_clip(native):
     lambda: synth.config_pulldown(nframes=100, width=320, height=180),
     lambda: synth.config_batched(nclips=1, length_range=(90, 90), resolutions=((256, 144),))[0],
 ])
-def test_library_detectors_equal_oracle_on_reduced_configs(native, maker):
-    got, ref = _offline(synth.Clip(maker()).frames())
+@pytest.mark.parametrize("prefetch", [0, 64])
+def test_library_detectors_equal_oracle_on_reduced_configs(native, maker, prefetch):
+    """With prefetch the speculative copy asks for more pairs; neither a
+    decision nor the reported measure set may change."""
+    got, ref = _offline(synth.Clip(maker()).frames(), prefetch_frames=prefetch)
     _same(got, ref)
 
 
