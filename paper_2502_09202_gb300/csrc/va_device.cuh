@@ -59,20 +59,23 @@ __device__ __forceinline__ void cp_async_wait_group1() { asm volatile("cp.async.
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Shared-memory window of one block at a refinement level of block side S
-// (radius 2): WR rows of RW words copied from the 4-byte boundary at or before
-// the window's first byte (candidate dx = -2).  Every block owns one region of
-// kRefineWinWords words that both levels use, so a block's lanes never touch
-// another block's window and the levels need no CTA barrier.
-constexpr int kRefineWinWords = 124;
+// (radius 2): WR rows of RW words copied in CB-byte pieces from the CB-byte
+// boundary at or before the window's first byte (candidate dx = -2); RW * 4
+// covers that offset (< CB) plus the S + 4 bytes the candidates reach.  Every
+// block owns one region of kRefineWinWords words that both levels use, so a
+// block's lanes never touch another block's window and the levels need no CTA
+// barrier.  Regions start 4 banks apart (164 = 4 mod 32): the 8 blocks of a
+// warp read their windows' rows from disjoint banks.
+constexpr int kRefineWinWords = 164;
 template <int S>
 struct RefineWin;
 template <>
 struct RefineWin<16> {
-  static constexpr int WR = 20, RW = 6;
+  static constexpr int WR = 20, RW = 8, CB = 8;
 };
 template <>
 struct RefineWin<8> {
-  static constexpr int WR = 12, RW = 4;
+  static constexpr int WR = 12, RW = 4, CB = 4;
 };
 
 // Lane layout of one block at a refinement level: LPB lanes per block, each
@@ -131,32 +134,49 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
   const int cx = 2 * (PHASE == 0 ? s_vx[bl] : pvx), cy = 2 * (PHASE == 0 ? s_vy[bl] : pvy);
   const int xw = (bx0 + bxl) * S + cx - RR;   // image position of candidate (-RR, -RR)
   const int yw = (by0 + byl) * S + cy - RR;
-  const int xa = xw & ~3, s8 = 8 * (xw & 3);
+  constexpr int CB = Wn::CB, CPR = 4 * Wn::RW / CB;   // bytes per copy, copies per window row
+  static_assert(CPR % LPB == 0 || LPB % CPR == 0, "copies split evenly over a block's lanes");
+  const int xa = xw & ~(CB - 1), s8 = 8 * (xw & 3);
+  const int off = (xw - xa) >> 2;             // word of the window's first byte
   static_assert(Wn::WR * Wn::RW <= kRefineWinWords, "window fits the block's region");
-  static_assert(!IGLOBAL || WPL == 2, "global I words are loaded in pairs");
+  static_assert(!IGLOBAL || WPL <= 2, "global I words are loaded one or two at a time");
   uint32_t* const win = s_win + bl * kRefineWinWords;
 
   // ---- staging ----------------------------------------------------------------
-  // The block's lanes copy each row together (lane t: words t, t + LPB, ...):
-  // a warp instruction reads contiguous bytes per block.  A window leaving the
-  // image horizontally is read clamp-to-edge, each lane its own rows.
+  // Lane t copies pieces t, t + LPB, ... of every window row (a warp
+  // instruction reads contiguous bytes per block).  Inside the image the row
+  // address advances by the pitch; rows above or below it are clamped; a
+  // window leaving the image horizontally is read byte by byte, clamp-to-edge.
   if (PHASE != 2 && valid) {
-    const bool inside = xa >= 0 && xa + 4 * Wn::RW <= Jl.w;
-    if (inside) {
-      const uint8_t* src = Jl.p + xa + 4 * t;
+    auto copy = [&](uint32_t* d, const uint8_t* g) {
+      if constexpr (CB == 8) cp_async8(d, g);
+      else cp_async4(d, g);
+    };
+    if (xa >= 0 && xa + 4 * Wn::RW <= Jl.w) {
+      if (yw >= 0 && yw + Wn::WR <= Jl.h) {
+        const uint8_t* row = Jl.p + (size_t)yw * Jl.pitch + xa;
 #pragma unroll 4
-      for (int r = 0; r < Wn::WR; r++) {
-        const uint8_t* row = src + (size_t)clampi(yw + r, 0, Jl.h - 1) * Jl.pitch;
+        for (int r = 0; r < Wn::WR; r++) {
 #pragma unroll
-        for (int c = 0; c < Wn::RW; c += LPB)
-          if (c + t < Wn::RW) cp_async4(win + r * Wn::RW + c + t, row + 4 * c);
+          for (int c = 0; c < CPR; c += LPB)
+            if (c + t < CPR) copy(win + r * Wn::RW + (c + t) * (CB / 4), row + (c + t) * CB);
+          row += Jl.pitch;
+        }
+      } else {
+#pragma unroll 4
+        for (int r = 0; r < Wn::WR; r++) {
+          const uint8_t* row = Jl.p + (size_t)clampi(yw + r, 0, Jl.h - 1) * Jl.pitch + xa;
+#pragma unroll
+          for (int c = 0; c < CPR; c += LPB)
+            if (c + t < CPR) copy(win + r * Wn::RW + (c + t) * (CB / 4), row + (c + t) * CB);
+        }
       }
     } else {
-#pragma unroll
+#pragma unroll 1
       for (int k = 0; k < Wn::WR / LPB; k++) {
         const int r = t + LPB * k;
         const uint8_t* row = Jl.p + (size_t)clampi(yw + r, 0, Jl.h - 1) * Jl.pitch;
-#pragma unroll
+#pragma unroll 1
         for (int c = 0; c < Wn::RW; c++) win[r * Wn::RW + c] = load4_clamped(row, xa + 4 * c, Jl.w);
       }
     }
@@ -169,9 +189,14 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
         const uint8_t* ib = Ig.p + (size_t)((by0 + byl) * S + h * RT) * Ig.pitch + (bx0 + bxl) * S + 4 * q0;
 #pragma unroll
         for (int i = 0; i < RT; i++) {
-          const uint2 v = __ldg(reinterpret_cast<const uint2*>(ib + (size_t)i * Ig.pitch));
-          gcol[0][i] = v.x;
-          gcol[1][i] = v.y;
+          if constexpr (WPL == 2) {
+            const uint2 v = __ldg(reinterpret_cast<const uint2*>(ib));
+            gcol[0][i] = v.x;
+            gcol[WPL - 1][i] = v.y;
+          } else {
+            gcol[0][i] = __ldg(reinterpret_cast<const uint32_t*>(ib));
+          }
+          ib += Ig.pitch;
         }
       }
     }
@@ -201,7 +226,7 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
 #pragma unroll
           for (int i = 0; i < RT; i++) icol[m][i] = ip[i * IW + m];
       }
-      const uint32_t* wp = win + (h * RT) * Wn::RW + q0;
+      const uint32_t* wp = win + (h * RT) * Wn::RW + q0 + off;
 #pragma unroll
       for (int w = 0; w < RT + 2 * RR; w++) {
         uint32_t wv[WPL + 2], u[WPL + 1];
@@ -273,17 +298,22 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
         // of row i + dy_i
         const int o = (xw & 3) + r % 5, dyi = r / 5, sh = 8 * (o & 3);
         uint32_t si = 0, sj = 0, sii = 0, sjj = 0, sij = 0, sab = 0;
-        const uint32_t* ip = s_i + (byl * S + h * RT) * IW + bxl * NQ + q0;
+        const uint32_t* ip = IGLOBAL ? nullptr : s_i + (byl * S + h * RT) * IW + bxl * NQ + q0;
 #pragma unroll
         for (int m = 0; m < WPL; m++) {
-          const uint32_t* jp = win + (h * RT + dyi) * Wn::RW + q0 + m + (o >> 2);
+          const uint32_t* jp = win + (h * RT + dyi) * Wn::RW + q0 + m + off + (o >> 2);
+          const uint8_t* ig = IGLOBAL ? Ig.p + (size_t)((by0 + byl) * S + h * RT) * Ig.pitch + (bx0 + bxl) * S + 4 * (q0 + m)
+                                      : nullptr;
 #pragma unroll
           for (int i = 0; i < RT; i++) {
             // reread (the I words need no registers across the keys): staged tile, or L1
-            const uint32_t iv =
-                IGLOBAL ? __ldg(reinterpret_cast<const uint32_t*>(Ig.p + (size_t)((by0 + byl) * S + h * RT + i) * Ig.pitch +
-                                                                  (bx0 + bxl) * S + 4 * (q0 + m)))
-                        : ip[i * IW + m];
+            uint32_t iv;
+            if constexpr (IGLOBAL) {
+              iv = __ldg(reinterpret_cast<const uint32_t*>(ig));
+              ig += Ig.pitch;
+            } else {
+              iv = ip[i * IW + m];
+            }
             const uint32_t w0 = jp[i * Wn::RW], w1 = sh ? jp[i * Wn::RW + 1] : 0u;
             const uint32_t jv = __funnelshift_r(w0, w1, sh);
             si = __dp4a(iv, 0x01010101u, si);

@@ -259,7 +259,7 @@ pair_kernel(const PairBatch b) {
   __shared__ unsigned long long s_red[S::NW][kRecWords];
   __shared__ PairJob s_job[2];
   // refinement windows: level side 16 with radius 2 is the largest fast case
-  __shared__ uint32_t s_win[NB * kRefineWinWords];
+  __shared__ __align__(16) uint32_t s_win[NB * kRefineWinWords];
   // I tiles of levels 0 and 1 (fast path: 3 levels, radius 2), staged asynchronously
   __shared__ __align__(16) uint32_t s_i0[2][TBY * 16 * TBX * 4];
   __shared__ __align__(16) uint32_t s_i1[2][TBY * 8 * TBX * 2];

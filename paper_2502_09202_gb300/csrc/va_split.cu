@@ -114,10 +114,8 @@ template <int TBX, int TBY>
 __global__ void __launch_bounds__(RefineShape<TBX, TBY>::NT, RefineShape<TBX, TBY>::MINB) refine_kernel(const PairBatch b) {
   using S = RefineShape<TBX, TBY>;
   constexpr int NB = S::NB, NT = S::NT, LPB = S::LPB;
-  constexpr bool IG = LPB == 2;   // two lanes per block read their level-0 I words from global memory
-  __shared__ __align__(16) uint32_t s_i0[IG ? 4 : TBY * 16 * TBX * 4];
   __shared__ __align__(16) uint32_t s_i1[TBY * 8 * TBX * 2];
-  __shared__ uint32_t s_win[NB * kRefineWinWords];
+  __shared__ __align__(16) uint32_t s_win[NB * kRefineWinWords];
   __shared__ int s_vx[NB], s_vy[NB];
   __shared__ unsigned long long s_red[NT / 32][kRecWords];
   __shared__ PairJob s_job;
@@ -128,13 +126,6 @@ __global__ void __launch_bounds__(RefineShape<TBX, TBY>::NT, RefineShape<TBX, TB
   const int local = item - jb.item_begin;
   const int bx0 = (local % jb.tiles_x) * TBX, by0 = (local / jb.tiles_x) * TBY;
   const int nbx = jb.nbx, nby = jb.nby;
-  if constexpr (!IG) {
-    for (int c = tid; c < TBY * 16 * TBX; c += NT) {
-      const int r = c / TBX, k = c - r * TBX;
-      if (bx0 + k < nbx && by0 + r / 16 < nby)
-        cp_async16(&s_i0[c * 4], jb.I[0].p + (size_t)(by0 * 16 + r) * jb.I[0].pitch + (bx0 + k) * 16);
-    }
-  }
   for (int c = tid; c < TBY * 8 * TBX; c += NT) {
     const int r = c / TBX, k = c - r * TBX;
     if (bx0 + k < nbx && by0 + r / 8 < nby)
@@ -156,7 +147,8 @@ __global__ void __launch_bounds__(RefineShape<TBX, TBY>::NT, RefineShape<TBX, TB
   __syncthreads();
   refine_level<8, 2, NT, NB, TBX, false, 2, LPB>(jb.J[1], s_i1, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part,
                                                  tid, pv.x, pv.y);
-  refine_level<16, 2, NT, NB, TBX, true, 0, LPB, IG>(jb.J[0], s_i0, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part,
+  // level 0 reads its I words from global memory (no staged tile)
+  refine_level<16, 2, NT, NB, TBX, true, 0, LPB, true>(jb.J[0], nullptr, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part,
                                                      tid, 0, 0, jb.I[0]);
   __syncthreads();   // every block's vector is read below
   sums_phase<TBX, TBY, NT>(b, jb, bx0, by0, 16, true, part, s_vx, s_vy, s_red, tid);
