@@ -353,14 +353,15 @@ def run_batched(args):
     _warm_tiles(api, [(s.width, s.height) for s in specs])
 
     def plain_pass():
-        out, launches = [], 0
+        out, launches, pair_launches = [], 0, 0
         for s, f in zip(specs, clips):
             with api.Analyser(s.width, s.height, s.fps, **args.overrides) as a:
                 a.push(f)
                 a.finish()
                 out.append(a.results())
                 launches += a.stats()["launches"]
-        return out, launches
+                pair_launches += a.profile()["pair_launches"]
+        return out, (launches, pair_launches)
 
     def batched_pass():
         srv = api.Server(budget_bytes=int(args.budget_gb * (1 << 30)), **args.overrides)
@@ -388,9 +389,10 @@ def run_batched(args):
         "mode": "batched", "metric": "frames/s (host frames in, results out)", "unit": "frames/s",
         "clips": len(specs), "frames": frames, "pixels": sum(s.pixels * s.nframes for s in specs),
         "length_range": [lo, hi], "resolutions": sorted({f"{s.width}x{s.height}" for s in specs}),
-        "plain": {"value": frames / t_plain, "seconds": t_plain, "launches": launches_plain},
+        "plain": {"value": frames / t_plain, "seconds": t_plain, "launches": launches_plain[0],
+                  "pair_launches": launches_plain[1]},
         "batched": {"value": frames / t_batched, "seconds": t_batched, "launches": prof["launches"],
-                    "waves": prof["waves"], "pairs": prof["pairs"]},
+                    "pair_launches": prof["pair_launches"], "waves": prof["waves"], "pairs": prof["pairs"]},
         "speedup": t_plain / t_batched, "identical_outputs": same}))
     return 0
 
@@ -468,8 +470,8 @@ def run_served(args):
         "slowest": [{"request": int(i), "arrival_s": round(reqs[i][0], 4), "frames": len(clips[i]),
                      "size": f"{reqs[i][1].width}x{reqs[i][1].height}", "latency_s": round(float(lat[i]), 5)}
                     for i in np.argsort(-lat)[:5]],
-        "waves": prof["waves"], "launches": prof["launches"], "pairs": prof["pairs"],
-        "identical_to_alone": same, "checked": len(check)}))
+        "waves": prof["waves"], "launches": prof["launches"], "pair_launches": prof["pair_launches"],
+        "pairs": prof["pairs"], "identical_to_alone": same, "checked": len(check)}))
     return 0
 
 

@@ -64,7 +64,8 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=()) -> str:
         o = os.path.join(BUILD, s + ".o")
         objs.append(o)
         jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math", "-Wall",
-                     "-Wno-unused-function", *inc, "-c", os.path.join(CSRC, s), "-o", o])
+                     "-Wno-unused-function", *[f for f in extra_nvcc if f.startswith("-D")], *inc, "-c",
+                     os.path.join(CSRC, s), "-o", o])
     with ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
         outs = list(ex.map(_run, jobs))
     if verbose:

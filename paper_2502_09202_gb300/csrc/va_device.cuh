@@ -114,11 +114,18 @@ struct RefineLanes {
 // (pvx, pvy): a kernel can then issue the first level's copies together with
 // its other loads and wait once.
 // With IGLOBAL the I words come from the level's plane in global memory
-// (Ig, two words per lane as one 8-byte load) instead of a staged tile s_i.
-template <int S, int RR, int NT, int NB, int TBX, bool SUMS, int PHASE = 0, int LPB = 4, bool IGLOBAL = false>
+// (Ig, one or two words per lane and row) instead of a staged tile s_i; they
+// are loaded with the window copies and kept in registers (*icp carries them
+// from PHASE 1 to PHASE 2).
+struct ICols {
+  uint32_t v[2][16];
+};
+template <int S, int RR, int NT, int NB, int TBX, bool SUMS, int PHASE = 0, int LPB = 4, bool IGLOBAL = false,
+          int WINW = kRefineWinWords>
 __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i, int bx0, int by0, int nbx, int nby,
                                              int lam, int* s_vx, int* s_vy, uint32_t* s_win, uint32_t (&part)[6],
-                                             int tid, int pvx = 0, int pvy = 0, const Plane Ig = Plane{}) {
+                                             int tid, int pvx = 0, int pvy = 0, const Plane Ig = Plane{},
+                                             ICols* icp = nullptr) {
   static_assert(RR == 2, "candidate ranks and window shapes assume radius 2");
   using Wn = RefineWin<S>;
   using Ln = RefineLanes<S, LPB>;
@@ -138,9 +145,8 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
   static_assert(CPR % LPB == 0 || LPB % CPR == 0, "copies split evenly over a block's lanes");
   const int xa = xw & ~(CB - 1), s8 = 8 * (xw & 3);
   const int off = (xw - xa) >> 2;             // word of the window's first byte
-  static_assert(Wn::WR * Wn::RW <= kRefineWinWords, "window fits the block's region");
-  static_assert(!IGLOBAL || WPL <= 2, "global I words are loaded one or two at a time");
-  uint32_t* const win = s_win + bl * kRefineWinWords;
+  static_assert(Wn::WR * Wn::RW <= WINW, "window fits the block's region");
+  uint32_t* const win = s_win + bl * WINW;
 
   // ---- staging ----------------------------------------------------------------
   // Lane t copies pieces t, t + LPB, ... of every window row (a warp
@@ -181,25 +187,27 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
       }
     }
   }
-  if constexpr (PHASE != 1) {   // the rest computes (PHASE 1 only copies)
-    // I words of the lane from global memory, in flight while the window copies land
-    uint32_t gcol[IGLOBAL ? WPL : 1][IGLOBAL ? RT : 1];
-    if constexpr (IGLOBAL) {
-      if (valid) {
-        const uint8_t* ib = Ig.p + (size_t)((by0 + byl) * S + h * RT) * Ig.pitch + (bx0 + bxl) * S + 4 * q0;
+  ICols ic_local;
+  ICols& ic = *(PHASE == 0 ? &ic_local : icp);
+  static_assert(!IGLOBAL || (WPL <= 2 && RT <= 16), "a lane's I words fit ICols");
+  if constexpr (IGLOBAL && PHASE != 2) {
+    // the lane's I words, in flight while the window copies land
+    if (valid) {
+      const uint8_t* ib = Ig.p + (size_t)((by0 + byl) * S + h * RT) * Ig.pitch + (bx0 + bxl) * S + 4 * q0;
 #pragma unroll
-        for (int i = 0; i < RT; i++) {
-          if constexpr (WPL == 2) {
-            const uint2 v = __ldg(reinterpret_cast<const uint2*>(ib));
-            gcol[0][i] = v.x;
-            gcol[WPL - 1][i] = v.y;
-          } else {
-            gcol[0][i] = __ldg(reinterpret_cast<const uint32_t*>(ib));
-          }
-          ib += Ig.pitch;
+      for (int i = 0; i < RT; i++) {
+        if constexpr (WPL == 2) {
+          const uint2 v = __ldg(reinterpret_cast<const uint2*>(ib));
+          ic.v[0][i] = v.x;
+          ic.v[1][i] = v.y;
+        } else {
+          ic.v[0][i] = __ldg(reinterpret_cast<const uint32_t*>(ib));
         }
+        ib += Ig.pitch;
       }
     }
+  }
+  if constexpr (PHASE != 1) {   // the rest computes (PHASE 1 only copies)
     if constexpr (PHASE == 0) {
       cp_async_commit();
       cp_async_wait_all();
@@ -218,7 +226,7 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
 #pragma unroll
         for (int m = 0; m < WPL; m++)
 #pragma unroll
-          for (int i = 0; i < RT; i++) icol[m][i] = gcol[m][i];
+          for (int i = 0; i < RT; i++) icol[m][i] = ic.v[m][i];
       } else {
         const uint32_t* ip = s_i + (byl * S + h * RT) * IW + bxl * NQ + q0;
 #pragma unroll
@@ -302,18 +310,10 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
 #pragma unroll
         for (int m = 0; m < WPL; m++) {
           const uint32_t* jp = win + (h * RT + dyi) * Wn::RW + q0 + m + off + (o >> 2);
-          const uint8_t* ig = IGLOBAL ? Ig.p + (size_t)((by0 + byl) * S + h * RT) * Ig.pitch + (bx0 + bxl) * S + 4 * (q0 + m)
-                                      : nullptr;
 #pragma unroll
           for (int i = 0; i < RT; i++) {
-            // reread (the I words need no registers across the keys): staged tile, or L1
-            uint32_t iv;
-            if constexpr (IGLOBAL) {
-              iv = __ldg(reinterpret_cast<const uint32_t*>(ig));
-              ig += Ig.pitch;
-            } else {
-              iv = ip[i * IW + m];
-            }
+            // the lane's I words again: registers, or reread from the staged tile
+            const uint32_t iv = IGLOBAL ? ic.v[m][i] : ip[i * IW + m];
             const uint32_t w0 = jp[i * Wn::RW], w1 = sh ? jp[i * Wn::RW + 1] : 0u;
             const uint32_t jv = __funnelshift_r(w0, w1, sh);
             si = __dp4a(iv, 0x01010101u, si);
