@@ -528,8 +528,11 @@ def run_gpu(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e0.record(stream)
+        dev_step_ms = []
         for _ in range(args.steps):
+            t_s = time.perf_counter()
             res, prof = one_step_device(time_kernels=1)
+            dev_step_ms.append(round(1e3 * (time.perf_counter() - t_s), 3))
             profs.append(prof)
         e1.record(stream)
         torch.cuda.synchronize()
@@ -545,9 +548,11 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2.record(stream)
-    hprofs = []
+    hprofs, host_step_ms = [], []
     for _ in range(args.steps):
+        t_s = time.perf_counter()
         hres, hprof = one_step_host()
+        host_step_ms.append(round(1e3 * (time.perf_counter() - t_s), 3))
         hprofs.append(hprof)
     e3.record(stream)
     torch.cuda.synchronize()
@@ -579,7 +584,8 @@ def run_gpu(args):
                    "param_overrides": args.overrides},
         "e2e": {"value": e2e_value, "unit": "frames/s", "ms_per_step": ms_e2e,
                 "h2d_bytes_per_step": int(hprofs[-1]["h2d_bytes"]), "d2h_bytes_per_step": int(hprofs[-1]["d2h_bytes"]),
-                "h2d_link_gbs": link_gbs},
+                "h2d_link_gbs": link_gbs, "host_step_ms": host_step_ms},
+        "step_ms": dev_step_ms,
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": "pair_kernel", "achieved": achieved, "peak": sad_peak,
                      "unit": "T|a-b|/s", "frac": (achieved / sad_peak) if achieved else None,
@@ -591,6 +597,8 @@ def run_gpu(args):
                      "hbm_peak_gbs": peaks.get("hbm_gbs")},
         "host_ms_per_step": {k: sum(p[k] for p in profs) / args.steps for k in
                              ("host_gather_ms", "host_wait_ms", "host_results_ms", "host_setup_ms")},
+        "e2e_host_ms": [{k: round(p[k], 3) for k in ("host_gather_ms", "host_wait_ms", "host_results_ms",
+                                                      "host_setup_ms", "host_copy_wait_ms")} for p in hprofs],
         "clocks": clk.summary(),
     }
     if hres["cuts"] != res["cuts"] or hres["dissolves"] != res["dissolves"]:

@@ -236,6 +236,7 @@ typedef struct {
   double host_wait_ms;                       /* host time waiting for wave completion */
   double host_results_ms;                    /* host time finalising records and running detectors */
   double host_setup_ms;                      /* host time creating the analyser (window allocation, tables) */
+  double host_copy_wait_ms;                  /* host time blocked on frame copies from host memory */
 } analyser_profile_t;
 int analyser_profile(const analyser* a, analyser_profile_t* out);
 

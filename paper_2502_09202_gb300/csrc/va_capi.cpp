@@ -480,6 +480,21 @@ int server_step(server* s, int* active) {
     return 0;
   };
   if (land(false)) return fail_srv(s, e.status, e.message);
+  // every wave costs a host round trip: while copies are still landing and no
+  // detector waits for pairs, let at least kMinWave new frames (over all clips)
+  // accumulate before launching
+  constexpr int kMinWave = 64;
+  for (;;) {
+    int fresh = 0, pending = 0;
+    bool copying = false;
+    for (va::Clip* c : e.clips) {
+      fresh += c->pushed - c->pyr_done;
+      pending += (int)c->pending.size();
+      copying = copying || !c->up_chunks.empty();
+    }
+    if (!copying || pending > 0 || fresh >= kMinWave) break;
+    if (land(true)) return fail_srv(s, e.status, e.message);
+  }
   int rc = e.wave();
   if (rc < 0 || e.status) return fail_srv(s, e.status ? e.status : rc, e.message);
   bool in_flight = false;

@@ -226,6 +226,7 @@ void Engine::profile(analyser_profile_t* out) const {
   out->host_wait_ms = host_wait_ms;
   out->host_results_ms = host_results_ms;
   out->host_setup_ms = host_setup_ms;
+  out->host_copy_wait_ms = host_copy_wait_ms;
 }
 
 int Engine::init(std::string& why) {
@@ -380,7 +381,10 @@ int Engine::poll_uploads(Clip* c, bool wait) {
   const int before = c->pushed;
   while (!c->up_chunks.empty()) {
     cudaEvent_t ev = c->up_chunks.front().second;
-    cudaError_t e = wait && c->pushed == before ? wait_event(ev) : cudaEventQuery(ev);
+    const bool block = wait && c->pushed == before;
+    const double tq = block ? now_seconds() : 0.0;
+    cudaError_t e = block ? wait_event(ev) : cudaEventQuery(ev);
+    if (block) host_copy_wait_ms += 1e3 * (now_seconds() - tq);
     if (e == cudaErrorNotReady) {
       cudaGetLastError();
       break;
@@ -465,7 +469,7 @@ void Engine::choose_tile(int width, int height, int* tbx, int* tby) {
       if (add_clip(&c, why, false) == ANALYSER_OK) {
         attach_device(&c, d, pitch, stride, nfr);
         const int cand[5][2] = {{8, 4}, {4, 4}, {8, 2}, {16, 2}, {4, 8}};
-        double best_s = 1e30;
+        double best_s = 1e30, t84 = -1.0;
         for (auto& cd : cand) {
           if (!pair_tile_supported(p.radius_coarse, cd[0], cd[1])) continue;
           c.tbx = cd[0];
@@ -482,7 +486,11 @@ void Engine::choose_tile(int width, int height, int* tbx, int* tby) {
             if (it > 0) tsum += t1 - t0;
           }
           if (ok && tsum < best_s) { best_s = tsum; bx = cd[0]; by = cd[1]; }
+          if (ok && cd[0] == 8 && cd[1] == 4) t84 = tsum;
         }
+        // the default shape unless another is clearly faster: clips of several
+        // sizes then share one launch per wave
+        if (t84 > 0.0 && t84 <= 1.03 * best_s) { bx = 8; by = 4; }
         cudaStreamSynchronize(stream);
         pool_free(c.d_ring);
         c.d_ring = nullptr;
@@ -702,7 +710,8 @@ int Engine::wave_launch() {
   // also a chunk of the wave, so that chunk c's refinement runs beside chunk
   // c+1's coarse search
   const bool split = p.levels == 3 && p.radius_refine == 2 && p.kernel_mode == 0;
-  const int chunk = split ? std::max(4, (npairs + 3) / 4) : npairs + 1;
+  // (four chunks for a large wave; a small one is not worth the launches)
+  const int chunk = split && npairs >= 256 ? (npairs + 3) / 4 : npairs + 1;
   size_t cvec_total = 0;
   for (auto& w : wp_) {
     const Geometry& g = w.clip->geo;

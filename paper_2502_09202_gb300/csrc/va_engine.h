@@ -146,7 +146,7 @@ class Engine {
   long long n_pair_launches = 0, n_pyr_launches = 0;
   double pair_ms = 0.0, pyr_ms = 0.0, absdiff_ops = 0.0, pyr_bytes = 0.0;
   long long h2d_bytes = 0, d2h_bytes = 0;
-  double host_gather_ms = 0, host_wait_ms = 0, host_results_ms = 0, host_setup_ms = 0;
+  double host_gather_ms = 0, host_wait_ms = 0, host_results_ms = 0, host_setup_ms = 0, host_copy_wait_ms = 0;
   void profile(analyser_profile_t* out) const;
   int status = ANALYSER_OK;
   std::string message;

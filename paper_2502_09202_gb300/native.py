@@ -75,7 +75,7 @@ class Profile(ctypes.Structure):
                 ("pyramid_launches", c_ll), ("pair_kernel_ms", c_double), ("pyramid_kernel_ms", c_double),
                 ("absdiff_ops", c_double), ("pyramid_bytes", c_double), ("h2d_bytes", c_ll), ("d2h_bytes", c_ll),
                 ("host_gather_ms", c_double), ("host_wait_ms", c_double), ("host_results_ms", c_double),
-                ("host_setup_ms", c_double)]
+                ("host_setup_ms", c_double), ("host_copy_wait_ms", c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
