@@ -236,6 +236,19 @@ def run_reference(args):
     return 0
 
 
+def run_sad(args):
+    """|a-b| accumulate rate of each packed sequence in the same register-only
+    loop (the candidates for the kernels' instruction and the ALU roofline)."""
+    import torch
+    from paper_2502_09202_gb300 import api
+    torch.cuda.set_device(0)
+    names = ["vabsdiff4 with accumulate", "sum-of-absolute-differences + add", "absolute differences + dp4a",
+             "max - min + dp4a", "half vabsdiff4.add, half absdiff + dp4a"]
+    rates = {names[q]: max(api.sad_sequence_rate(q, 0) for _ in range(max(1, args.steps))) for q in range(5)}
+    print(json.dumps({"mode": "sad", "unit": "T |a-b|/s", "best_of": max(1, args.steps), "rates": rates}))
+    return 0
+
+
 def run_kernel(args):
     """Pair-kernel timing: `--pairs` consecutive 1080p frame pairs of the workload
     through analyser_measure_pairs on torch's current stream (CUDA events)."""
@@ -635,7 +648,7 @@ def main():
     ap.add_argument("--ref-frames", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--window", type=int, default=512, help="frames resident per clip (1.7 GB at 1080p)")
-    ap.add_argument("--mode", default="clip", choices=["clip", "kernel", "batched", "served", "configs"])
+    ap.add_argument("--mode", default="clip", choices=["clip", "kernel", "batched", "served", "configs", "sad"])
     ap.add_argument("--clips", type=int, default=64)
     ap.add_argument("--requests", type=int, default=512)
     ap.add_argument("--rate", type=float, default=40.0)
@@ -650,6 +663,8 @@ def main():
         return run_reference(args)
     if args.mode == "kernel":
         return run_kernel(args)
+    if args.mode == "sad":
+        return run_sad(args)
     if args.mode == "batched":
         return run_batched(args)
     if args.mode == "served":

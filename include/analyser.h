@@ -304,6 +304,16 @@ int analyser_detect_offline(const analyser_params* p, int width, int height, int
 int analyser_measure_sad_peak(int device, double* tera_per_s);
 
 /*
+ * The same register-only loop timed for other packed |a-b| sequences (for
+ * choosing the kernels' instruction): 0 vabsdiff4 with accumulate (as
+ * analyser_measure_sad_peak), 1 the sum-of-absolute-differences intrinsic plus
+ * an add, 2 per-byte absolute differences plus dp4a, 3 per-byte max minus min
+ * plus dp4a, 4 half the chains as 0 and half as 2.  Same units and errors as
+ * analyser_measure_sad_peak; a sequence outside 0..4 gives ANALYSER_ERR_INVALID_ARG.
+ */
+int analyser_measure_sad_sequence(int device, int sequence, double* tera_per_s);
+
+/*
  * Resource cache (the paper has no counterpart: this is library plumbing).
  * Device buffers, page-locked host buffers, streams and events that an
  * analyser, server or analyser_measure_pairs call releases go back to a

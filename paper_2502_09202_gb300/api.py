@@ -14,7 +14,7 @@ from . import native as N
 from .native import AnalyserError, default_params
 
 __all__ = ["Analyser", "Server", "measure_pairs", "detect_offline", "default_params", "AnalyserError",
-           "results_to_dict", "sad_peak", "MeasureTable", "trim_cache"]
+           "results_to_dict", "sad_peak", "sad_sequence_rate", "MeasureTable", "trim_cache"]
 
 
 def _check(code: int, where: str, handle=None):
@@ -219,6 +219,15 @@ def sad_peak(device: int = 0) -> float:
     """Measured packed-SAD throughput of this GPU, 10^12 |a-b| accumulates per second."""
     v = ctypes.c_double()
     _check(N.lib.analyser_measure_sad_peak(device, ctypes.byref(v)), "analyser_measure_sad_peak")
+    return v.value
+
+
+def sad_sequence_rate(sequence: int, device: int = 0) -> float:
+    """|a-b| accumulates per second (T/s) of packed sequence `sequence` (0..4)
+    in the peak loop: 0 vabsdiff4 with accumulate, 1 sum-of-absolute-differences
+    plus add, 2 absolute differences plus dp4a, 3 max - min plus dp4a, 4 half and half of 0 and 2."""
+    v = ctypes.c_double()
+    _check(N.lib.analyser_measure_sad_sequence(device, sequence, ctypes.byref(v)), "analyser_measure_sad_sequence")
     return v.value
 
 

@@ -5,6 +5,13 @@
 namespace va {
 
 // ---------------------------------------------------------------------------
+// barrier of the threads running a tile's code (the whole CTA)
+// ---------------------------------------------------------------------------
+struct CtaBarrier {
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+
+// ---------------------------------------------------------------------------
 // packed-byte primitives
 // ---------------------------------------------------------------------------
 
@@ -267,9 +274,9 @@ __device__ __forceinline__ void refine_level(const Plane Jl, const uint32_t* s_i
       pk[j] = acc[c0 % 5][c0 / 5] | (c1 < 25 ? acc[c1 % 5][c1 / 5] << 16 : 0u);
     }
 #pragma unroll
-    for (int off = 1; off < LPB; off <<= 1) {
+    for (int xo = 1; xo < LPB; xo <<= 1) {
 #pragma unroll
-      for (int j = 0; j < 13; j++) pk[j] += __shfl_xor_sync(0xFFFFFFFFu, pk[j], off);
+      for (int j = 0; j < 13; j++) pk[j] += __shfl_xor_sync(0xFFFFFFFFu, pk[j], xo);
     }
     uint32_t best = 0xFFFFFFFFu;
     if (valid) {
@@ -470,10 +477,10 @@ __device__ __forceinline__ void coarse_phase(const uint32_t* jwin, const uint32_
 // pixels (added during the level-0 refinement) and only the strips beyond the
 // last full block column/row are read here; otherwise every pixel of the tile
 // is read here.
-template <int TBX, int TBY, int NT>
+template <int TBX, int TBY, int NT, class Bar = CtaBarrier>
 __device__ __forceinline__ void sums_phase(const PairBatch& b, const PairJob& jb, int bx0, int by0, int B0, bool fast,
                                            const uint32_t (&part)[6], const int* s_vx, const int* s_vy,
-                                           unsigned long long (*s_red)[kRecWords], int tid) {
+                                           unsigned long long (*s_red)[kRecWords], int tid, const Bar& bar = Bar{}) {
   constexpr int NB = TBX * TBY, NW = NT / 32;
   const int nbx = jb.nbx, nby = jb.nby;
   const Plane I0 = jb.I[0], J0 = jb.J[0];
@@ -552,13 +559,13 @@ __device__ __forceinline__ void sums_phase(const PairBatch& b, const PairJob& jb
 #pragma unroll
     for (int k = 0; k < kRecWords; k++) s_red[warp][k] = v[k];
   }
-  __syncthreads();
+  bar.sync();
   if (tid < kRecWords) {
     unsigned long long a = 0;
     for (int w = 0; w < NW; w++) a += s_red[w][tid];
     atomicAdd(jb.rec + tid, a);
   }
-  __syncthreads();
+  bar.sync();
 }
 
 }  // namespace va

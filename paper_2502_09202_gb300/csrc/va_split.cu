@@ -44,33 +44,52 @@ struct RefineShape {
 // Copies the job holding `item` to shared memory: thread t checks jobs t,
 // t + NT, ... at once (item_begin[j] <= item < item_begin[j + 1]; exactly one
 // job matches, also with empty jobs), so the lookup costs one round trip to L2 whatever the
-// number of jobs.  Called by the whole CTA; ends with a barrier.
-template <int NT>
-__device__ __forceinline__ void copy_job(const PairBatch& b, int item, PairJob* dst, int* s_jidx, int tid) {
+// number of jobs.  Called by every thread of `bar`; ends with a barrier.
+template <int NT, class Bar>
+__device__ __forceinline__ void copy_job(const PairBatch& b, int item, PairJob* dst, int* s_jidx, int tid,
+                                         const Bar& bar) {
   for (int j = tid; j < b.njobs; j += NT) {
     const int beg = b.jobs[j].item_begin;
     const int next = j + 1 < b.njobs ? b.jobs[j + 1].item_begin : 0x7FFFFFFF;
     if ((j == 0 || beg <= item) && item < next) *s_jidx = j;   // item_begin is nondecreasing: one match
   }
-  __syncthreads();
+  bar.sync();
   const int* src = reinterpret_cast<const int*>(b.jobs + *s_jidx);
   for (int i = tid; i < (int)(sizeof(PairJob) / 4); i += NT) reinterpret_cast<int*>(dst)[i] = src[i];
-  __syncthreads();
+  bar.sync();
 }
 
+// Shared memory of one coarse tile and of one refinement tile.
 template <int R, int TBX, int TBY>
-__global__ void __launch_bounds__(CoarseShape<R, TBX, TBY>::NT, CoarseShape<R, TBX, TBY>::MINB) coarse_kernel(const PairBatch b) {
+struct CoarseSmem {
   using S = CoarseShape<R, TBX, TBY>;
-  constexpr int NB = S::NB, NT = S::NT, WROWS = S::WROWS, WWORDS = S::WWORDS;
-  __shared__ uint32_t s_jwin[4 * WROWS * WWORDS];   // the window shifted by 0..3 bytes
-  __shared__ uint32_t s_iw[TBY * kCoarseSide * TBX];
-  __shared__ uint32_t s_best32[NB];
-  __shared__ int s_vx[NB], s_vy[NB];
-  __shared__ PairJob s_job;
-  __shared__ int s_jidx;
-  const int tid = threadIdx.x, item = blockIdx.x;
-  copy_job<NT>(b, item, &s_job, &s_jidx, tid);
-  const PairJob& jb = s_job;
+  uint32_t jwin[4 * S::WROWS * S::WWORDS];   // the window shifted by 0..3 bytes
+  uint32_t iw[TBY * kCoarseSide * TBX];
+  uint32_t best32[S::NB];
+  int vx[S::NB], vy[S::NB];
+  PairJob job;
+  int jidx;
+};
+template <int TBX, int TBY>
+struct RefineSmem {
+  using S = RefineShape<TBX, TBY>;
+  alignas(16) uint32_t i1[TBY * 8 * TBX * 2];
+  alignas(16) uint32_t win[S::NB * kRefineWinWords];
+  int vx[S::NB], vy[S::NB];
+  unsigned long long red[S::NT / 32][kRecWords];
+  PairJob job;
+  int jidx;
+};
+
+// Exhaustive coarse search of one tile by NT threads (the whole CTA, NT >= the
+// shape's thread count); vectors written to the pair's coarse-vector array.
+template <int R, int TBX, int TBY, int NT>
+__device__ __forceinline__ void coarse_tile(const PairBatch& b, int item, CoarseSmem<R, TBX, TBY>& sm, int tid) {
+  using S = CoarseShape<R, TBX, TBY>;
+  constexpr int NB = S::NB, WROWS = S::WROWS, WWORDS = S::WWORDS;
+  static_assert(NT >= S::NT, "enough threads for the coarse layout");
+  copy_job<NT>(b, item, &sm.job, &sm.jidx, tid, CtaBarrier{});
+  const PairJob& jb = sm.job;
   const int local = item - jb.item_begin;
   const int bx0 = (local % jb.tiles_x) * TBX, by0 = (local / jb.tiles_x) * TBY;
   const int nbx = jb.nbx, nby = jb.nby;
@@ -88,48 +107,44 @@ __global__ void __launch_bounds__(CoarseShape<R, TBX, TBY>::NT, CoarseShape<R, T
       w0 = load4_clamped(row, x, J2.w);
       w1 = load4_clamped(row, x + 4, J2.w);
     }
-    s_jwin[c] = w0;
-    s_jwin[WROWS * WWORDS + c] = __funnelshift_r(w0, w1, 8);
-    s_jwin[2 * WROWS * WWORDS + c] = __funnelshift_r(w0, w1, 16);
-    s_jwin[3 * WROWS * WWORDS + c] = __funnelshift_r(w0, w1, 24);
+    sm.jwin[c] = w0;
+    sm.jwin[WROWS * WWORDS + c] = __funnelshift_r(w0, w1, 8);
+    sm.jwin[2 * WROWS * WWORDS + c] = __funnelshift_r(w0, w1, 16);
+    sm.jwin[3 * WROWS * WWORDS + c] = __funnelshift_r(w0, w1, 24);
   }
   for (int c = tid; c < TBY * kCoarseSide * TBX; c += NT) {
     const int r = c / TBX, k = c - r * TBX;
-    s_iw[c] = (bx0 + k < nbx && by0 + r / kCoarseSide < nby)
-                  ? __ldg(reinterpret_cast<const uint32_t*>(I2.p + (size_t)(by0 * kCoarseSide + r) * I2.pitch +
-                                                            (bx0 + k) * kCoarseSide))
-                  : 0u;
+    sm.iw[c] = (bx0 + k < nbx && by0 + r / kCoarseSide < nby)
+                   ? __ldg(reinterpret_cast<const uint32_t*>(I2.p + (size_t)(by0 * kCoarseSide + r) * I2.pitch +
+                                                             (bx0 + k) * kCoarseSide))
+                   : 0u;
   }
-  for (int i = tid; i < NB; i += NT) s_best32[i] = 0xFFFFFFFFu;
+  for (int i = tid; i < NB; i += NT) sm.best32[i] = 0xFFFFFFFFu;
   __syncthreads();
-  coarse_phase<R, TBX, TBY, NT, true>(s_jwin, s_iw, bx0, by0, nbx, nby, b.cfg.lambda, b.cfg.key_mul, s_best32, s_vx,
-                                       s_vy, tid);
+  coarse_phase<R, TBX, TBY, NT, true>(sm.jwin, sm.iw, bx0, by0, nbx, nby, b.cfg.lambda, b.cfg.key_mul, sm.best32,
+                                       sm.vx, sm.vy, tid);
   for (int i = tid; i < NB; i += NT) {
     const int bx = bx0 + i % TBX, by = by0 + i / TBX;
-    if (bx < nbx && by < nby) jb.cvec[(size_t)by * nbx + bx] = make_short2((short)s_vx[i], (short)s_vy[i]);
+    if (bx < nbx && by < nby) jb.cvec[(size_t)by * nbx + bx] = make_short2((short)sm.vx[i], (short)sm.vy[i]);
   }
 }
 
-template <int TBX, int TBY>
-__global__ void __launch_bounds__(RefineShape<TBX, TBY>::NT, RefineShape<TBX, TBY>::MINB) refine_kernel(const PairBatch b) {
+// Both refinement levels, the AMM term and the motion-compensated sums of one
+// tile by the shape's NT threads, which synchronise through `bar`.
+template <int TBX, int TBY, class Bar>
+__device__ __forceinline__ void refine_tile(const PairBatch& b, int item, RefineSmem<TBX, TBY>& sm, int tid,
+                                            const Bar& bar) {
   using S = RefineShape<TBX, TBY>;
   constexpr int NB = S::NB, NT = S::NT, LPB = S::LPB;
-  __shared__ __align__(16) uint32_t s_i1[TBY * 8 * TBX * 2];
-  __shared__ __align__(16) uint32_t s_win[NB * kRefineWinWords];
-  __shared__ int s_vx[NB], s_vy[NB];
-  __shared__ unsigned long long s_red[NT / 32][kRecWords];
-  __shared__ PairJob s_job;
-  __shared__ int s_jidx;
-  const int tid = threadIdx.x, item = blockIdx.x;
-  copy_job<NT>(b, item, &s_job, &s_jidx, tid);
-  const PairJob& jb = s_job;
+  copy_job<NT>(b, item, &sm.job, &sm.jidx, tid, bar);
+  const PairJob& jb = sm.job;
   const int local = item - jb.item_begin;
   const int bx0 = (local % jb.tiles_x) * TBX, by0 = (local / jb.tiles_x) * TBY;
   const int nbx = jb.nbx, nby = jb.nby;
   for (int c = tid; c < TBY * 8 * TBX; c += NT) {
     const int r = c / TBX, k = c - r * TBX;
     if (bx0 + k < nbx && by0 + r / 8 < nby)
-      cp_async8(&s_i1[c * 2], jb.I[1].p + (size_t)(by0 * 8 + r) * jb.I[1].pitch + (bx0 + k) * 8);
+      cp_async8(&sm.i1[c * 2], jb.I[1].p + (size_t)(by0 * 8 + r) * jb.I[1].pitch + (bx0 + k) * 8);
   }
   // each lane reads its block's coarse vector and issues its level-1 window
   // copies now, so that the tile's loads all land behind one wait
@@ -140,18 +155,30 @@ __global__ void __launch_bounds__(RefineShape<TBX, TBY>::NT, RefineShape<TBX, TB
     const int bl = tid / LPB, bx = bx0 + bl % TBX, by = by0 + bl / TBX;
     if (bl < NB && bx < nbx && by < nby) pv = jb.cvec[(size_t)by * nbx + bx];
   }
-  refine_level<8, 2, NT, NB, TBX, false, 1, LPB>(jb.J[1], s_i1, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part,
-                                                 tid, pv.x, pv.y);
+  refine_level<8, 2, NT, NB, TBX, false, 1, LPB>(jb.J[1], sm.i1, bx0, by0, nbx, nby, lam, sm.vx, sm.vy, sm.win,
+                                                 part, tid, pv.x, pv.y);
   cp_async_commit();
   cp_async_wait_all();
-  __syncthreads();
-  refine_level<8, 2, NT, NB, TBX, false, 2, LPB>(jb.J[1], s_i1, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part,
-                                                 tid, pv.x, pv.y);
+  bar.sync();
+  refine_level<8, 2, NT, NB, TBX, false, 2, LPB>(jb.J[1], sm.i1, bx0, by0, nbx, nby, lam, sm.vx, sm.vy, sm.win,
+                                                 part, tid, pv.x, pv.y);
   // level 0 reads its I words from global memory (no staged tile)
-  refine_level<16, 2, NT, NB, TBX, true, 0, LPB, true>(jb.J[0], nullptr, bx0, by0, nbx, nby, lam, s_vx, s_vy, s_win, part,
-                                                     tid, 0, 0, jb.I[0]);
-  __syncthreads();   // every block's vector is read below
-  sums_phase<TBX, TBY, NT>(b, jb, bx0, by0, 16, true, part, s_vx, s_vy, s_red, tid);
+  refine_level<16, 2, NT, NB, TBX, true, 0, LPB, true>(jb.J[0], nullptr, bx0, by0, nbx, nby, lam, sm.vx, sm.vy,
+                                                       sm.win, part, tid, 0, 0, jb.I[0]);
+  bar.sync();   // every block's vector is read below
+  sums_phase<TBX, TBY, NT>(b, jb, bx0, by0, 16, true, part, sm.vx, sm.vy, sm.red, tid, bar);
+}
+
+template <int R, int TBX, int TBY>
+__global__ void __launch_bounds__(CoarseShape<R, TBX, TBY>::NT, CoarseShape<R, TBX, TBY>::MINB) coarse_kernel(const PairBatch b) {
+  __shared__ CoarseSmem<R, TBX, TBY> sm;
+  coarse_tile<R, TBX, TBY, CoarseShape<R, TBX, TBY>::NT>(b, blockIdx.x, sm, threadIdx.x);
+}
+
+template <int TBX, int TBY>
+__global__ void __launch_bounds__(RefineShape<TBX, TBY>::NT, RefineShape<TBX, TBY>::MINB) refine_kernel(const PairBatch b) {
+  __shared__ RefineSmem<TBX, TBY> sm;
+  refine_tile<TBX, TBY>(b, blockIdx.x, sm, threadIdx.x, CtaBarrier{});
 }
 
 }  // namespace

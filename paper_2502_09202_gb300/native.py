@@ -101,6 +101,7 @@ SIGNATURES = {
     "analyser_measure_pair_noalloc": (c_int, [P(Params), c_int, c_int, c_int, VP, VP, c_ll, P(c_i64), VP]),
     "analyser_detect_offline": (c_int, [P(Params), c_int, c_int, c_int, MEASURE_FN, VP, P(VP)]),
     "analyser_measure_sad_peak": (c_int, [c_int, P(c_double)]),
+    "analyser_measure_sad_sequence": (c_int, [c_int, c_int, P(c_double)]),
     "analyser_trim_cache": (None, []),
     "analyser_cached_bytes": (c_ll, []),
     "server_create": (c_int, [P(Params), c_ull, P(VP)]),

@@ -260,6 +260,28 @@ def test_split_and_fused_kernels_match_the_oracle(mode):
         _compare_results(a.results(), OA.analyse_frames(frames))
 
 
+def test_chunked_wave_matches_the_oracle():
+    """A call of 300 pairs runs as 4 chunks: the coarse kernel of chunk c+1
+    beside the refinement kernel of chunk c on the second stream.  Every
+    pair's record and motion field equal the oracle's, at a ragged size, pairs
+    of every kind."""
+    api = _api()
+    w, h = 333, 190
+    clip = synth.Clip(synth.ClipSpec(w, h, 12, 25.0, synth.TFF, 9, 3.0,
+                                     synth.SceneStyle(n_objects=(4, 6), obj_speed=10, cell=8, bg_kind="textured")))
+    frames = clip.frames()
+    rng = np.random.default_rng(7)
+    n = 300
+    kinds = [int(k) for k in rng.integers(0, 5, n)]
+    ia = [int(a) for a in rng.integers(0, 12, n)]
+    ib = [int(b) for b in rng.integers(0, 12, n)]
+    rec, mot = api.measure_pairs(_dev(frames), kinds, ia, ib, want_motion=True)
+    for k in range(n):
+        ref, vec = _oracle_pair(kinds[k], frames[ia[k]], frames[ib[k]])
+        assert list(rec[k]) == [ref[f] for f in REC7], k
+        assert np.array_equal(mot[k], vec), k
+
+
 def test_cached_buffers_reused_across_clips_and_trimmed():
     """Analysers and stateless calls created one after another run on buffers the
     previous ones returned to the resource cache (not cleared): results stay
@@ -367,3 +389,17 @@ def test_served_requests_match_the_oracle():
     for t, f in zip(tickets, clips):
         _compare_results(srv.poll(t), OA.analyse_frames(f))
     srv.close()
+
+
+def test_packed_sequence_rates_are_measured():
+    """Each packed |a-b| sequence of the peak loop runs and gives a positive
+    rate; sequence 0 is analyser_measure_sad_peak's; a sequence outside 0..4 is
+    refused without device work."""
+    import ctypes
+    from paper_2502_09202_gb300 import native as N
+    api = _api()
+    rates = [api.sad_sequence_rate(q, 0) for q in range(5)]
+    assert all(r > 0 for r in rates)
+    v = ctypes.c_double()
+    assert N.lib.analyser_measure_sad_sequence(0, 5, ctypes.byref(v)) == N.ERR_INVALID_ARG
+    assert N.lib.analyser_measure_sad_sequence(0, 0, None) == N.ERR_INVALID_ARG
