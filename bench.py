@@ -27,10 +27,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "interlaced-tff-1920x1080x1500@25fps"
-# dram__bytes_read.sum + dram__bytes_write.sum of coarse_kernel + refine_kernel for 16 frame
-# pairs of this workload (one ncu --set full capture of `--mode kernel --pairs 64`), per pair;
-# to be re-taken whenever either kernel changes
-PAIR_KERNEL_DRAM_BYTES_PER_PAIR = (2.236928e6 + 45.086720e6 + 0.170240e6) / 16
+# dram__bytes_read.sum + dram__bytes_write.sum of coarse_kernel + refine_kernel for 64 frame
+# pairs of this workload (one launch each in an ncu --set full capture of `--mode kernel
+# --pairs 64`), per pair; to be re-taken whenever either kernel changes
+PAIR_KERNEL_DRAM_BYTES_PER_PAIR = (8.469504e6 + 0.0 + 170.572288e6 + 3.480832e6) / 64
 METRIC = "frames/s at 1080p luma (full analysis: measures + decisions)"
 
 

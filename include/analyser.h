@@ -329,7 +329,12 @@ long long analyser_cached_bytes(void);
 
 /* ---- serving: continuous batching of many clips on one GPU ------------------- */
 
-/* A server admits clips while the device-memory budget allows. */
+/* A server admits clips while the device-memory budget allows.  Every clip of
+ * a server uses one tile shape (params tile_x/tile_y, else 8x4; no autotune),
+ * so that a wave's pairs of all sizes go out as one coarse and one refinement
+ * launch; while frame copies are landing and no detector waits for pairs, a
+ * step waits for 1024 new frames (over all clips) or the end of the copies
+ * before it launches a wave. */
 int server_create(const analyser_params* p, unsigned long long budget_bytes, server** out);
 
 /*

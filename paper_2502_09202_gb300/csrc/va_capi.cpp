@@ -381,6 +381,11 @@ int server_create(const analyser_params* p, unsigned long long budget_bytes, ser
   s->eng.reset(new (std::nothrow) va::Engine(*p));
   if (!s->eng) { delete s; return ANALYSER_ERR_OOM; }
   rc = s->eng->init(why);
+  // one tile shape for every clip (8x4 unless the parameters fix one): a wave's
+  // pairs of all sizes then go out as one coarse and one refinement launch
+  // (a tile changes the schedule only, never a result)
+  s->eng->autotune = false;
+  s->eng->max_chunks = 1;
   if (rc) { delete s; return rc; }
   *out = s;
   return ANALYSER_OK;
@@ -483,7 +488,7 @@ int server_step(server* s, int* active) {
   // every wave costs a host round trip: while copies are still landing and no
   // detector waits for pairs, let at least kMinWave new frames (over all clips)
   // accumulate before launching
-  constexpr int kMinWave = 64;
+  constexpr int kMinWave = 1024;
   for (;;) {
     int fresh = 0, pending = 0;
     bool copying = false;

@@ -425,6 +425,11 @@ static std::mutex g_tune_mu;
 static std::map<std::vector<int>, std::pair<int, int>> g_tune;
 
 void Engine::choose_tile(int width, int height, int* tbx, int* tby) {
+  if (!autotune) {   // the default shape, whatever other engines of the process tuned
+    *tbx = 8;
+    *tby = 4;
+    return;
+  }
   int dev = 0;
   cudaGetDevice(&dev);
   const std::vector<int> gkey = {dev, width, height, p.levels, p.radius_coarse, p.radius_refine};
@@ -711,7 +716,8 @@ int Engine::wave_launch() {
   // c+1's coarse search
   const bool split = p.levels == 3 && p.radius_refine == 2 && p.kernel_mode == 0;
   // (four chunks for a large wave; a small one is not worth the launches)
-  const int chunk = split && npairs >= 256 ? (npairs + 3) / 4 : npairs + 1;
+  const int nchunks = split && npairs >= 256 ? std::max(1, max_chunks) : 1;
+  const int chunk = split ? (npairs + nchunks - 1) / nchunks : npairs + 1;
   size_t cvec_total = 0;
   for (auto& w : wp_) {
     const Geometry& g = w.clip->geo;

@@ -151,6 +151,7 @@ class Engine {
   int status = ANALYSER_OK;
   std::string message;
   bool autotune = true;
+  int max_chunks = 4;        // chunks of a large wave (coarse of chunk c+1 beside refinement of chunk c)
 
  private:
   int ensure_capacity(int npairs, int ndown, int npyr);
