@@ -358,13 +358,6 @@ __device__ __forceinline__ uint32_t coarse_rows(const uint32_t* wrow, uint32_t i
   // of the block at window row dy, starts at k = 0 and completes at k = 3.
   uint32_t acc[NJ][4];
   uint32_t best[NJ], pend[NJ];   // pend: the previous row's keys, folded in pairs by a 3-input minimum
-#if defined(VA_COARSE_FMIN)
-  // keys + 2^23 are the bit patterns of positive normal floats, which order as
-  // the integers do: the minimum runs as a float minimum
-  float bestf[NJ], pendf[NJ];
-#pragma unroll
-  for (int j = 0; j < NJ; j++) bestf[j] = pendf[j] = __uint_as_float(0x7F7FFFFFu);
-#endif
 #pragma unroll
   for (int j = 0; j < NJ; j++) {
     best[j] = 0xFFFFFFFFu;
@@ -393,33 +386,15 @@ __device__ __forceinline__ uint32_t coarse_rows(const uint32_t* wrow, uint32_t i
     if (dy >= 3) {
       const int vy = dy - R - 3;
       const int avy = vy < 0 ? -vy : vy;
-#if defined(VA_COARSE_FMIN)
-      const uint32_t bv = lamM * (uint32_t)avy + ((((uint32_t)avy << 12) | ((uint32_t)(vy + R) << 6)) + 0x00800000u);
-#else
       const uint32_t bv = lamM * (uint32_t)avy + (((uint32_t)avy << 12) | ((uint32_t)(vy + R) << 6));
-#endif
 #pragma unroll
       for (int j = 0; j < NJ; j++) {
         const uint32_t key = acc[j][(dy - 3) & 3] * keyM + bv;
-#if defined(VA_COARSE_FMIN)
-        if (((dy - 3) & 1) == 0 && dy < 2 * R + 3) pendf[j] = __uint_as_float(key);
-        else bestf[j] = fminf(bestf[j], fminf(pendf[j], __uint_as_float(key)));
-#elif defined(VA_COARSE_NOPEND)
-        best[j] = min(best[j], key);
-#elif defined(VA_COARSE_MIN2)
-        if (((dy - 3) & 1) == 0 && dy < 2 * R + 3) pend[j] = key;
-        else best[j] = min(best[j], min(pend[j], key));
-#else
         if (((dy - 3) & 1) == 0 && dy < 2 * R + 3) pend[j] = key;
         else best[j] = __vimin3_u32(best[j], pend[j], key);
-#endif
       }
     }
   }
-#if defined(VA_COARSE_FMIN)
-#pragma unroll
-  for (int j = 0; j < NJ; j++) best[j] = __float_as_uint(bestf[j]) - 0x00800000u;
-#endif
   uint32_t tbest = 0xFFFFFFFFu;
 #pragma unroll
   for (int j = 0; j < NJ; j++) {
