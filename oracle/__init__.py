@@ -13,6 +13,8 @@ Layout
   measures.py   ctypes wrapper, field extraction, FP64 finalisation (NCC, SWR, AMM, ACT)
   analyser.py   the detectors (shot fast/deep check, sampling structure,
                 dynamic keyframes) run sequentially over a whole clip
+  dis.py        the dense sub-pixel flow estimator (inverse search per patch,
+                coarse to fine, densification) in FP64 numpy
 
 Parity status: the integer measures are pinned by closed forms, invariants and
 brute force (tests/test_oracle_pins.py); the decisions are pinned by planted
