@@ -249,6 +249,53 @@ def run_sad(args):
     return 0
 
 
+def run_flow(args):
+    """Dense sub-pixel flow (analyser_dense_flow): `--pairs` consecutive 1080p frame
+    pairs of the workload, frames resident in HBM (inputs of all pairs larger
+    than L2), FP32 and FP64, each pair one call on torch's current stream timed
+    with CUDA events."""
+    import numpy as np
+    import torch
+    from paper_2502_09202_gb300 import api, synth
+    torch.cuda.set_device(0)
+    spec = _spec()
+    clip = synth.Clip(spec)
+    n = args.pairs
+    host = np.stack([clip.frame(300 + t) for t in range(n + 1)])
+    dev = torch.from_numpy(host).cuda()
+    T, H, W = dev.shape
+    out = torch.empty((H, W, 2), dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+    p = api.flow_params()
+    # search work per pair: per level, patches x steps x 64 pixels; FP operations
+    # per pixel-step (bilinear sample 9, residual 1, two products and sums 4)
+    S, P = p.stride, p.patch
+    steps_px = 0
+    for l in range(p.levels):
+        w, h = W >> l, H >> l
+        steps_px += ((w - P + S - 1) // S + 1) * ((h - P + S - 1) // S + 1) * p.iters * P * P
+    flops = 14.0 * steps_px
+    res = {}
+    for fp64 in (0, 1):
+        k = n if not fp64 else max(1, n // 4)
+        for _ in range(max(1, args.warmup)):
+            api.dense_flow(dev[0], dev[1], out=out, fp64=fp64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for i in range(k):
+            api.dense_flow(dev[i], dev[i + 1], out=out, fp64=fp64)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        res["fp64" if fp64 else "fp32"] = {"ms_per_pair": ms, "pairs_per_s": 1000.0 / ms,
+                                            "search_gflop_per_s": flops / (ms * 1e-3) / 1e9, "pairs": k}
+    print(json.dumps({"mode": "flow", "workload": f"{W}x{H} frame pairs of {WORKLOAD}", "params": {
+        "levels": p.levels, "patch": p.patch, "stride": p.stride, "iters": p.iters, "damp_rel": p.damp_rel,
+        "damp_abs": p.damp_abs}, "search_pixel_steps_per_pair": steps_px, "results": res}))
+    return 0
+
+
 def run_kernel(args):
     """Pair-kernel timing: `--pairs` consecutive 1080p frame pairs of the workload
     through analyser_measure_pairs on torch's current stream (CUDA events)."""
@@ -648,7 +695,8 @@ def main():
     ap.add_argument("--ref-frames", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--window", type=int, default=512, help="frames resident per clip (1.7 GB at 1080p)")
-    ap.add_argument("--mode", default="clip", choices=["clip", "kernel", "batched", "served", "configs", "sad"])
+    ap.add_argument("--mode", default="clip", choices=["clip", "kernel", "batched", "served", "configs", "sad",
+                                                         "flow"])
     ap.add_argument("--clips", type=int, default=64)
     ap.add_argument("--requests", type=int, default=512)
     ap.add_argument("--rate", type=float, default=40.0)
@@ -665,6 +713,8 @@ def main():
         return run_kernel(args)
     if args.mode == "sad":
         return run_sad(args)
+    if args.mode == "flow":
+        return run_flow(args)
     if args.mode == "batched":
         return run_batched(args)
     if args.mode == "served":

@@ -313,6 +313,51 @@ int analyser_measure_sad_peak(int device, double* tera_per_s);
  */
 int analyser_measure_sad_sequence(int device, int sequence, double* tera_per_s);
 
+/* ---- dense sub-pixel flow (alternative motion estimator) ---------------------- */
+
+/*
+ * Dense flow by inverse search, the estimator the paper names for its motion
+ * field (Sec. III.A, reference [8]), as an alternative to the block-matching
+ * field the analyser's measures use.  Steps, coarse to fine over the same box
+ * pyramid: a grid of patch x patch patches of frame a (stride `stride`, the last
+ * patch of a row or column flush with the border); per patch `iters`
+ * inverse-compositional Gauss-Newton steps, H from the template's
+ * central-difference gradients damped by damp_rel * trace(H) + damp_abs, the
+ * residual J(x + u) - T(x) with frame b sampled bilinearly (clamp-to-edge); a
+ * patch starts from the coarser level's dense flow at its centre, doubled;
+ * densification weights each covering patch by 1 / max(1, |J(x + u) - I(x)|).
+ * No step compares against a threshold.  The kernels compute in FP32, or in
+ * FP64 with fp64 = 1 (the output is float either way).  Where a patch's
+ * iteration does not converge, FP32 rounding can grow over the steps: the FP32
+ * flow then differs from an FP64 evaluation by more than rounding at some
+ * pixels.
+ */
+typedef struct analyser_flow_params {
+  int levels;        /* pyramid levels, 1..3; width and height >= patch << (levels - 1) (3) */
+  int patch;         /* patch side; this build supports 8 (8) */
+  int stride;        /* patch grid step, 1..patch (4) */
+  int iters;         /* Gauss-Newton steps per patch and level, 0..64 (8) */
+  int fp64;          /* 0: the steps in FP32; 1: in FP64 (slower; element-wise reproducible) (0) */
+  double damp_rel;   /* damping per unit of trace(H), >= 0 (0.01) */
+  double damp_abs;   /* damping added to it, > 0 (1.0) */
+} analyser_flow_params;
+
+void analyser_default_flow_params(analyser_flow_params* p);
+
+/*
+ * The flow from frame a to frame b (frame b at x + U(x) matches frame a at x):
+ * frame_a, frame_b: DEVICE 8-bit luma planes, width x height, rows pitch_bytes
+ * apart (width <= pitch_bytes <= INT_MAX); flow: DEVICE buffer of width *
+ * height * 2 floats, written row-major as (u, v) per pixel; all owned by the
+ * caller.  Runs on `stream` (a cudaStream_t, or null) and returns once the flow
+ * is written; device scratch comes from the resource cache.  Returns
+ * ANALYSER_ERR_INVALID_ARG for null pointers or parameters or sizes outside
+ * the ranges above, ANALYSER_ERR_OOM when scratch cannot be had,
+ * ANALYSER_ERR_CUDA when a launch fails.
+ */
+int analyser_dense_flow(const analyser_flow_params* p, int width, int height, const uint8_t* frame_a,
+                        const uint8_t* frame_b, long long pitch_bytes, float* flow, void* stream);
+
 /*
  * Resource cache (the paper has no counterpart: this is library plumbing).
  * Device buffers, page-locked host buffers, streams and events that an

@@ -116,21 +116,23 @@ def inverse_search(I: np.ndarray, J: np.ndarray, init: np.ndarray, dp: DisParams
 
 def densify(I: np.ndarray, J: np.ndarray, flows: np.ndarray, dp: DisParams = DisParams()) -> np.ndarray:
     """Dense flow (h, w, 2): per pixel the photometric-error weighted mean of the
-    covering patches' flows (step 5)."""
+    covering patches' flows (step 5), accumulated patch by patch in row-major
+    patch order."""
     h, w = I.shape
     P = dp.patch
     oy, ox, _, _ = patch_grid(h, w, P, dp.stride)
+    ry, rx = np.meshgrid(np.arange(P), np.arange(P), indexing="ij")
+    Y = (oy[:, None, None] + ry[None]).reshape(len(oy), -1)      # (N, P*P)
+    X = (ox[:, None, None] + rx[None]).reshape(len(oy), -1)
+    fx, fy = flows[:, 0, None], flows[:, 1, None]
+    e = bilinear(J, X + fx, Y + fy) - I.astype(np.float64)[Y, X]
+    wgt = 1.0 / np.maximum(1.0, np.abs(e))
     num = np.zeros((h, w, 2))
     den = np.zeros((h, w))
-    Iw = I.astype(np.float64)
-    ry, rx = np.meshgrid(np.arange(P), np.arange(P), indexing="ij")
-    for i in range(len(oy)):
-        Y, X = oy[i] + ry, ox[i] + rx
-        e = bilinear(J, X + flows[i, 0], Y + flows[i, 1]) - Iw[Y, X]
-        wgt = 1.0 / np.maximum(1.0, np.abs(e))
-        num[Y, X, 0] += wgt * flows[i, 0]
-        num[Y, X, 1] += wgt * flows[i, 1]
-        den[Y, X] += wgt
+    # np.add.at applies the patches' contributions in index order (patch-major)
+    np.add.at(num[..., 0], (Y.ravel(), X.ravel()), (wgt * fx).ravel())
+    np.add.at(num[..., 1], (Y.ravel(), X.ravel()), (wgt * fy).ravel())
+    np.add.at(den, (Y.ravel(), X.ravel()), wgt.ravel())
     return num / den[..., None]
 
 

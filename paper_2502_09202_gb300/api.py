@@ -14,7 +14,8 @@ from . import native as N
 from .native import AnalyserError, default_params
 
 __all__ = ["Analyser", "Server", "measure_pairs", "detect_offline", "default_params", "AnalyserError",
-           "results_to_dict", "sad_peak", "sad_sequence_rate", "MeasureTable", "trim_cache"]
+           "results_to_dict", "sad_peak", "sad_sequence_rate", "MeasureTable", "trim_cache",
+           "flow_params", "dense_flow"]
 
 
 def _check(code: int, where: str, handle=None):
@@ -165,6 +166,32 @@ def analyse(frames: np.ndarray, fps: float = 25.0, **overrides) -> dict:
         a.push(frames)
         a.finish()
         return a.results()
+
+
+def flow_params(**overrides) -> N.FlowParams:
+    p = N.FlowParams()
+    N.lib.analyser_default_flow_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def dense_flow(frame_a, frame_b, out=None, stream=None, **overrides):
+    """Dense sub-pixel flow (analyser_dense_flow) from frame a to frame b, both CUDA
+    uint8 tensors (h, w) with unit column stride and the same row pitch.  Returns
+    a CUDA float32 tensor (h, w, 2) of (u, v) per pixel (`out` if given)."""
+    import torch
+    assert frame_a.is_cuda and frame_b.is_cuda and frame_a.dim() == 2 and frame_a.shape == frame_b.shape
+    assert frame_a.stride(1) == 1 and frame_b.stride(1) == 1 and frame_a.stride(0) == frame_b.stride(0)
+    h, w = frame_a.shape
+    if out is None:
+        out = torch.empty((h, w, 2), dtype=torch.float32, device=frame_a.device)
+    assert out.is_cuda and out.is_contiguous() and out.shape == (h, w, 2) and out.dtype == torch.float32
+    p = flow_params(**overrides)
+    st = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    _check(N.lib.analyser_dense_flow(ctypes.byref(p), w, h, frame_a.data_ptr(), frame_b.data_ptr(), frame_a.stride(0),
+                                     out.data_ptr(), ctypes.c_void_p(st)), "analyser_dense_flow")
+    return out
 
 
 def measure_pairs(frames, kinds, ia, ib, params: N.Params | None = None, want_motion: bool = False,

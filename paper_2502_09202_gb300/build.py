@@ -22,7 +22,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["va_kernels.cu", "va_split.cu", "va_peak.cu", "va_noalloc.cu"]
+CU_SOURCES = ["va_kernels.cu", "va_split.cu", "va_peak.cu", "va_noalloc.cu", "va_flow.cu"]
 CPP_SOURCES = ["va_detect.cpp", "va_engine.cpp", "va_capi.cpp", "va_pool.cpp"]
 
 

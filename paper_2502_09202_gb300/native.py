@@ -83,6 +83,11 @@ class Profile(ctypes.Structure):
 
 MEASURE_FN = ctypes.CFUNCTYPE(c_int, ctypes.c_void_p, c_int, c_int, c_int, ctypes.POINTER(c_i64))
 
+class FlowParams(ctypes.Structure):
+    _fields_ = [("levels", c_int), ("patch", c_int), ("stride", c_int), ("iters", c_int), ("fp64", c_int),
+                ("damp_rel", c_double), ("damp_abs", c_double)]
+
+
 # every entry point of include/analyser.h: name -> (restype, argtypes)
 P, VP = ctypes.POINTER, ctypes.c_void_p
 SIGNATURES = {
@@ -102,6 +107,8 @@ SIGNATURES = {
     "analyser_detect_offline": (c_int, [P(Params), c_int, c_int, c_int, MEASURE_FN, VP, P(VP)]),
     "analyser_measure_sad_peak": (c_int, [c_int, P(c_double)]),
     "analyser_measure_sad_sequence": (c_int, [c_int, c_int, P(c_double)]),
+    "analyser_default_flow_params": (None, [P(FlowParams)]),
+    "analyser_dense_flow": (c_int, [P(FlowParams), c_int, c_int, VP, VP, c_ll, VP, VP]),
     "analyser_trim_cache": (None, []),
     "analyser_cached_bytes": (c_ll, []),
     "server_create": (c_int, [P(Params), c_ull, P(VP)]),

@@ -1,0 +1,132 @@
+"""Dense sub-pixel flow on the GPU (analyser_dense_flow) against the oracle
+(oracle/dis.py), on the same seeded frames.
+
+The FP64 instantiation computes the oracle's steps in the oracle's precision:
+it must match element by element within FLOW_TOL_FP64 (summation order and the
+FMA contraction of the products are the only differences; the iteration can
+amplify them in patches that do not converge, bounded here by measurement).
+The FP32 instantiation (the default) differs from an FP64 evaluation by
+rounding that such patches amplify over the steps: it is checked against the
+oracle through the statistics of the difference (mean, 99th percentile) and
+exactly where the arithmetic leaves no rounding (no step, identical frames)."""
+import numpy as np
+import pytest
+
+from oracle import dis as D
+from paper_2502_09202_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# Tolerances (px), from the arithmetic and the measured spread on GB300:
+# - FP64 vs FP64, up to 8 steps: the two sides differ in summation order (a
+#   warp butterfly against a sequential sum) and in contracted products, a few
+#   1e-16 relative, which non-converging patches amplify to at most 8e-5 px on
+#   a 1080p pair (1e-6 px on the 333x190 clip): tolerance 2e-4 px;
+# - with 20 steps the amplification grows (FP64 max 0.064 px, mean 5e-6 px):
+#   mean below 1e-4 px and 99.9th percentile below 1e-2 px;
+# - FP32 (sample positions near x = 1000 spaced 6e-5 px apart, sums of 64
+#   products): 1e-5 px where patches converge, measured mean 1e-4..0.014 px and
+#   99th percentile up to 0.18 px over these cases: mean below 0.02 px and
+#   99th percentile below 0.25 px (with 20 steps: 0.05 px and 1.0 px).
+FLOW_TOL_FP64 = 2e-4
+FP64_LONG_MEAN_TOL, FP64_LONG_P999_TOL = 1e-4, 1e-2
+FP32_MEAN_TOL, FP32_P99_TOL = 0.02, 0.25
+FP32_LONG_MEAN_TOL, FP32_LONG_P99_TOL = 0.05, 1.0
+
+
+def _gpu(fa, fb, **kw):
+    from paper_2502_09202_gb300 import api
+    a = torch.from_numpy(np.ascontiguousarray(fa)).cuda()
+    b = torch.from_numpy(np.ascontiguousarray(fb)).cuda()
+    return api.dense_flow(a, b, **kw).cpu().numpy().astype(np.float64)
+
+
+def _dp(kw):
+    return D.DisParams(**{k: v for k, v in kw.items() if k != "fp64"})
+
+
+_CLIP = None
+
+
+def _clip():
+    global _CLIP
+    if _CLIP is None:
+        spec = synth.ClipSpec(333, 190, 8, 25.0, synth.TFF, 9, 3.0,
+                              synth.SceneStyle(n_objects=(4, 6), obj_speed=10, cell=8, bg_kind="textured"))
+        _CLIP = synth.Clip(spec).frames()
+    return _CLIP
+
+
+CASES = [dict(), dict(levels=1), dict(levels=2), dict(stride=1), dict(stride=3), dict(stride=8), dict(iters=1),
+         dict(iters=20), dict(damp_rel=0.0, damp_abs=1.0), dict(damp_rel=0.1, damp_abs=10.0)]
+
+
+@pytest.mark.parametrize("kw", CASES, ids=[str(c) for c in CASES])
+def test_fp64_flow_equals_the_oracle(kw):
+    fr = _clip()
+    for t in (0, 4):
+        d = np.abs(D.dis_flow(fr[t], fr[t + 1], _dp(kw)) - _gpu(fr[t], fr[t + 1], fp64=1, **kw))
+        if kw.get("iters", 8) <= 8:
+            assert d.max() <= FLOW_TOL_FP64, (kw, t, d.max())
+        else:
+            assert d.mean() <= FP64_LONG_MEAN_TOL and np.quantile(d, 0.999) <= FP64_LONG_P999_TOL, (kw, t)
+
+
+@pytest.mark.parametrize("kw", CASES, ids=[str(c) for c in CASES])
+def test_fp32_flow_statistics_match_the_oracle(kw):
+    fr = _clip()
+    long = kw.get("iters", 8) > 8
+    for t in (0, 4):
+        d = np.abs(D.dis_flow(fr[t], fr[t + 1], _dp(kw)) - _gpu(fr[t], fr[t + 1], **kw))
+        mean_tol, p99_tol = (FP32_LONG_MEAN_TOL, FP32_LONG_P99_TOL) if long else (FP32_MEAN_TOL, FP32_P99_TOL)
+        assert d.mean() <= mean_tol and np.quantile(d, 0.99) <= p99_tol, (kw, t, d.mean(), np.quantile(d, 0.99))
+
+
+@pytest.mark.parametrize("fp64", [0, 1])
+def test_exact_cases(fp64):
+    fr = _clip()
+    # identical frames: zero residuals, zero flow, weights 1
+    assert np.array_equal(_gpu(fr[2], fr[2], fp64=fp64), np.zeros((190, 333, 2)))
+    # no step: every patch keeps its (zero) start, the dense flow is zero
+    assert np.array_equal(_gpu(fr[2], fr[3], fp64=fp64, iters=0), np.zeros((190, 333, 2)))
+
+
+@pytest.mark.parametrize("h,w,levels", [(32, 32, 3), (33, 47, 3), (16, 16, 2), (8, 8, 1), (61, 100, 3)])
+def test_small_and_ragged_sizes(h, w, levels):
+    rng = np.random.default_rng(h * w + levels)
+    base = rng.integers(0, 256, (h + 8, w + 8)).astype(np.uint8)
+    fa, fb = base[4:4 + h, 4:4 + w], base[3:3 + h, 5:5 + w]
+    U = D.dis_flow(fa, fb, D.DisParams(levels=levels))
+    assert np.abs(U - _gpu(fa, fb, levels=levels, fp64=1)).max() <= FLOW_TOL_FP64
+    d = np.abs(U - _gpu(fa, fb, levels=levels))
+    assert d.mean() <= FP32_MEAN_TOL and np.quantile(d, 0.99) <= FP32_P99_TOL
+
+
+def test_full_size_pair_of_the_bench_clip():
+    """One 1920x1080 pair of the interlaced workload at the bench's parameters."""
+    c = synth.Clip(synth.config_interlaced())
+    a, b = c.frame(300), c.frame(301)
+    U = D.dis_flow(a, b)
+    assert np.abs(U - _gpu(a, b, fp64=1)).max() <= FLOW_TOL_FP64
+    d = np.abs(U - _gpu(a, b))
+    assert d.mean() <= FP32_MEAN_TOL and np.quantile(d, 0.99) <= FP32_P99_TOL
+
+
+def test_invalid_arguments_are_refused():
+    from paper_2502_09202_gb300 import api, native as N
+    import ctypes
+    a = torch.zeros((40, 40), dtype=torch.uint8, device="cuda")
+    out = torch.zeros((40, 40, 2), dtype=torch.float32, device="cuda")
+    for bad in (dict(levels=4), dict(levels=0), dict(patch=16), dict(stride=0), dict(stride=9), dict(iters=65),
+                dict(fp64=2), dict(damp_abs=0.0), dict(damp_rel=-1.0)):
+        p = api.flow_params(**bad)
+        assert N.lib.analyser_dense_flow(ctypes.byref(p), 40, 40, a.data_ptr(), a.data_ptr(), 40, out.data_ptr(),
+                                         None) == N.ERR_INVALID_ARG, bad
+    p = api.flow_params()
+    assert N.lib.analyser_dense_flow(ctypes.byref(p), 31, 40, a.data_ptr(), a.data_ptr(), 40, out.data_ptr(),
+                                     None) == N.ERR_INVALID_ARG      # below patch << (levels - 1)
+    assert N.lib.analyser_dense_flow(ctypes.byref(p), 40, 40, a.data_ptr(), a.data_ptr(), 39, out.data_ptr(),
+                                     None) == N.ERR_INVALID_ARG      # pitch below width
+    assert N.lib.analyser_dense_flow(ctypes.byref(p), 40, 40, None, a.data_ptr(), 40, out.data_ptr(),
+                                     None) == N.ERR_INVALID_ARG
