@@ -158,3 +158,34 @@ def dis_flow(fa: np.ndarray, fb: np.ndarray, dp: DisParams = DisParams()) -> np.
         flows = inverse_search(I, J, init, dp)
         U = densify(I, J, flows, dp)
     return U
+
+
+def flow_measure(fa: np.ndarray, fb: np.ndarray, dp: DisParams = DisParams()) -> dict:
+    """The pair measures of Sec. III.A with the dense flow U as the motion
+    field: AMM = mean |U(x)| over the n pixels; frame b warped by U,
+    Jw(x) = J(x + U(x)) (bilinear, clamp-to-edge); NCC of frame a and Jw from
+    the sums S_i, S_j, S_ii, S_jj, S_ij as C / sqrt(Vi * Vj) with C = n S_ij -
+    S_i S_j, Vi = n S_ii - S_i^2, Vj = n S_jj - S_j^2 (both variances zero or
+    below: 1, one of them: 0); SWR = max(0, 1 - NCC); ACT = sqrt(AMM * SWR)."""
+    U = dis_flow(fa, fb, dp)
+    h, w = fa.shape
+    yy, xx = np.mgrid[0:h, 0:w].astype(np.float64)
+    I = fa.astype(np.float64)
+    Jw = bilinear(fb, xx + U[..., 0], yy + U[..., 1])
+    n = float(h * w)
+    si, sj = I.sum(), Jw.sum()
+    sii, sjj, sij = (I * I).sum(), (Jw * Jw).sum(), (I * Jw).sum()
+    smag = np.sqrt(U[..., 0] ** 2 + U[..., 1] ** 2).sum()
+    c = n * sij - si * sj
+    vi = n * sii - si * si
+    vj = n * sjj - sj * sj
+    if vi <= 0.0 and vj <= 0.0:
+        ncc = 1.0
+    elif vi <= 0.0 or vj <= 0.0:
+        ncc = 0.0
+    else:
+        ncc = c / np.sqrt(vi * vj)
+    swr = max(0.0, 1.0 - ncc)
+    amm = smag / n
+    return {"amm": float(amm), "ncc": float(ncc), "swr": float(swr), "act": float(np.sqrt(amm * swr)),
+            "sums": [float(v) for v in (smag, si, sj, sii, sjj, sij)], "n": int(h * w)}

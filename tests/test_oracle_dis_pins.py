@@ -131,3 +131,39 @@ def test_smooth_image_subpixel_shift_is_recovered():
         c = U[16:-16, 16:-16]
         assert abs(c[..., 0].mean() - s[0]) < 0.02 and abs(c[..., 1].mean() - s[1]) < 0.02
         assert np.abs(c[..., 0] - s[0]).max() < 0.3 and np.abs(c[..., 1] - s[1]).max() < 0.3
+
+
+def test_flow_measure_reduces_to_plain_correlation_without_flow():
+    # no step: the flow is exactly zero, Jw = J, AMM = 0 and NCC is the plain
+    # correlation of the two frames (numpy's corrcoef)
+    rng = np.random.default_rng(11)
+    a = rng.integers(0, 256, (48, 64)).astype(np.uint8)
+    b = np.clip(a.astype(int) // 2 + rng.integers(0, 40, a.shape), 0, 255).astype(np.uint8)
+    m = D.flow_measure(a, b, D.DisParams(iters=0))
+    assert m["amm"] == 0.0 and m["act"] == 0.0
+    assert abs(m["ncc"] - np.corrcoef(a.ravel().astype(float), b.ravel().astype(float))[0, 1]) < 1e-12
+    assert abs(m["swr"] - (1.0 - m["ncc"])) < 1e-15
+    inv = (255 - a.astype(int)).astype(np.uint8)
+    m = D.flow_measure(a, inv, D.DisParams(iters=0))
+    assert abs(m["ncc"] + 1.0) < 1e-12 and abs(m["swr"] - 2.0) < 1e-12
+    flat = np.full_like(a, 7)
+    assert D.flow_measure(flat, flat, D.DisParams(iters=0))["ncc"] == 1.0
+    assert D.flow_measure(a, flat, D.DisParams(iters=0))["ncc"] == 0.0
+
+
+def test_flow_measure_of_identical_frames_and_of_a_shift():
+    rng = np.random.default_rng(5)
+    a = rng.integers(0, 256, (40, 56)).astype(np.uint8)
+    m = D.flow_measure(a, a)
+    assert m["amm"] == 0.0 and m["ncc"] == 1.0 and m["act"] == 0.0
+    h, w = 96, 160
+    yy, xx = np.mgrid[0:h, 0:w].astype(float)
+
+    def img(sx, sy):
+        X, Y = xx - sx, yy - sy
+        v = 128 + 50 * np.sin(X / 7.0) + 40 * np.cos(Y / 9.0) + 20 * np.sin((X + Y) / 5.0)
+        return np.clip(np.rint(v), 0, 255).astype(np.uint8)
+
+    m = D.flow_measure(img(0, 0), img(2.5, -1.25))
+    assert abs(m["amm"] - np.hypot(2.5, 1.25)) < 0.05      # mean |U| near the true |s| (borders included)
+    assert m["ncc"] > 0.99                                  # the warped frame matches
