@@ -288,8 +288,15 @@ def run_flow(args):
         e1.record(st)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / k
+        e0.record(st)
+        for i in range(k):
+            api.flow_measure(dev[i], dev[i + 1], fp64=fp64)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms_m = e0.elapsed_time(e1) / k
         res["fp64" if fp64 else "fp32"] = {"ms_per_pair": ms, "pairs_per_s": 1000.0 / ms,
-                                            "search_gflop_per_s": flops / (ms * 1e-3) / 1e9, "pairs": k}
+                                            "search_gflop_per_s": flops / (ms * 1e-3) / 1e9, "pairs": k,
+                                            "measure_ms_per_pair": ms_m}
     print(json.dumps({"mode": "flow", "workload": f"{W}x{H} frame pairs of {WORKLOAD}", "params": {
         "levels": p.levels, "patch": p.patch, "stride": p.stride, "iters": p.iters, "damp_rel": p.damp_rel,
         "damp_abs": p.damp_abs}, "search_pixel_steps_per_pair": steps_px, "results": res}))

@@ -359,6 +359,25 @@ int analyser_dense_flow(const analyser_flow_params* p, int width, int height, co
                         const uint8_t* frame_b, long long pitch_bytes, float* flow, void* stream);
 
 /*
+ * The pair measures of Sec. III.A with the dense flow U of analyser_dense_flow
+ * as the motion field: AMM = mean |U(x)| over the width * height pixels (px);
+ * frame b warped by U, Jw(x) = J(x + U(x)) (bilinear, clamp-to-edge); NCC of
+ * frame a and Jw = C / sqrt(Vi * Vj) with C = n S_ij - S_i S_j, Vi = n S_ii -
+ * S_i^2, Vj = n S_jj - S_j^2 (both variances zero or below: 1, one of them: 0);
+ * SWR = max(0, 1 - NCC); ACT = sqrt(AMM * SWR).  The sums are FP64, added in
+ * a fixed order (the same value on every call); the per-pixel values are in
+ * the flow's precision.  Arguments and errors as
+ * analyser_dense_flow (scratch for the flow comes from the resource cache).
+ */
+typedef struct analyser_flow_measure_t {
+  double amm, ncc, swr, act;
+  double sums[6];   /* sum |U|, S_i, S_j, S_ii, S_jj, S_ij */
+} analyser_flow_measure_t;
+
+int analyser_flow_measure(const analyser_flow_params* p, int width, int height, const uint8_t* frame_a,
+                          const uint8_t* frame_b, long long pitch_bytes, analyser_flow_measure_t* out, void* stream);
+
+/*
  * Resource cache (the paper has no counterpart: this is library plumbing).
  * Device buffers, page-locked host buffers, streams and events that an
  * analyser, server or analyser_measure_pairs call releases go back to a

@@ -15,7 +15,7 @@ from .native import AnalyserError, default_params
 
 __all__ = ["Analyser", "Server", "measure_pairs", "detect_offline", "default_params", "AnalyserError",
            "results_to_dict", "sad_peak", "sad_sequence_rate", "MeasureTable", "trim_cache",
-           "flow_params", "dense_flow"]
+           "flow_params", "dense_flow", "flow_measure"]
 
 
 def _check(code: int, where: str, handle=None):
@@ -192,6 +192,21 @@ def dense_flow(frame_a, frame_b, out=None, stream=None, **overrides):
     _check(N.lib.analyser_dense_flow(ctypes.byref(p), w, h, frame_a.data_ptr(), frame_b.data_ptr(), frame_a.stride(0),
                                      out.data_ptr(), ctypes.c_void_p(st)), "analyser_dense_flow")
     return out
+
+
+def flow_measure(frame_a, frame_b, stream=None, **overrides) -> dict:
+    """Pair measures (amm, ncc, swr, act, sums) of frame a and frame b with the dense
+    flow as the motion field (analyser_flow_measure); frames as for dense_flow."""
+    import torch
+    assert frame_a.is_cuda and frame_b.is_cuda and frame_a.dim() == 2 and frame_a.shape == frame_b.shape
+    assert frame_a.stride(1) == 1 and frame_b.stride(1) == 1 and frame_a.stride(0) == frame_b.stride(0)
+    h, w = frame_a.shape
+    p = flow_params(**overrides)
+    m = N.FlowMeasure()
+    st = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    _check(N.lib.analyser_flow_measure(ctypes.byref(p), w, h, frame_a.data_ptr(), frame_b.data_ptr(),
+                                       frame_a.stride(0), ctypes.byref(m), ctypes.c_void_p(st)), "analyser_flow_measure")
+    return {"amm": m.amm, "ncc": m.ncc, "swr": m.swr, "act": m.act, "sums": list(m.sums), "n": int(h * w)}
 
 
 def measure_pairs(frames, kinds, ia, ib, params: N.Params | None = None, want_motion: bool = False,

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <climits>
+#include <cmath>
 #include <cstdint>
 
 #include "../../include/analyser.h"
@@ -187,6 +188,56 @@ __global__ void flow_densify_kernel(U8Plane I, U8Plane J, const F* flows, int np
   }
 }
 
+// The pair measures' sums over the dense flow U (float (u, v) per pixel): per
+// pixel |U|, I(x) and Jw(x) = J(x + U(x)) (bilinear, clamp-to-edge, in F); a
+// block's threads stride over the pixels accumulating in FP64 and the block
+// writes its six partial sums (|U|, I, Jw, I^2, Jw^2, I Jw) to part[block]
+constexpr int kMeasureThreads = 256, kMeasureBlocks = 1024;
+template <typename F>
+__global__ void __launch_bounds__(kMeasureThreads) flow_measure_kernel(U8Plane I, U8Plane J, const float* flow,
+                                                                       double* part) {
+  __shared__ double red[kMeasureThreads / 32][6];
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  const long long n = (long long)I.w * I.h;
+  for (long long i = blockIdx.x * (long long)kMeasureThreads + threadIdx.x; i < n;
+       i += (long long)gridDim.x * kMeasureThreads) {
+    const int x = (int)(i % I.w), y = (int)(i / I.w);
+    const F u = F(flow[2 * i]), w = F(flow[2 * i + 1]);
+    const F iv = F(px(I, x, y));
+    const F jw = sample_u8(J, F(x) + u, F(y) + w);
+    v[0] += (double)sqrt(u * u + w * w);
+    v[1] += (double)iv;
+    v[2] += (double)jw;
+    v[3] += (double)iv * (double)iv;
+    v[4] += (double)jw * (double)jw;
+    v[5] += (double)iv * (double)jw;
+  }
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xFFFFFFFFu, v[k], off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < 6; k++) red[threadIdx.x >> 5][k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double s = 0.0;
+    for (int wp = 0; wp < kMeasureThreads / 32; wp++) s += red[wp][threadIdx.x];
+    part[6 * blockIdx.x + threadIdx.x] = s;
+  }
+}
+
+// sums[k] = the blocks' partials in block order (one thread per word): the
+// same value on every call
+__global__ void flow_sum_kernel(const double* part, int nblocks, double* sums) {
+  if (threadIdx.x >= 6) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; b++) s += part[6 * b + threadIdx.x];
+  sums[threadIdx.x] = s;
+}
+
 int patches_along(int n, int S) { return (n - kFlowPatch + S - 1) / S + 1; }
 
 template <typename F>
@@ -279,4 +330,55 @@ extern "C" int analyser_dense_flow(const analyser_flow_params* fp, int width, in
   const cudaStream_t st = (cudaStream_t)stream;
   return fp->fp64 ? dense_flow<double>(fp, width, height, frame_a, frame_b, pitch_bytes, flow, st)
                   : dense_flow<float>(fp, width, height, frame_a, frame_b, pitch_bytes, flow, st);
+}
+
+extern "C" int analyser_flow_measure(const analyser_flow_params* fp, int width, int height, const uint8_t* frame_a,
+                                     const uint8_t* frame_b, long long pitch_bytes, analyser_flow_measure_t* out,
+                                     void* stream) {
+  using namespace va;
+  if (!out) return ANALYSER_ERR_INVALID_ARG;
+  // the flow (float, w x h x 2), the blocks' partial sums and the six FP64
+  // sums in one cached buffer
+  const size_t flow_bytes = ((size_t)width * height * 2 * sizeof(float) + 255) / 256 * 256;
+  if (width <= 0 || height <= 0 || width > 16384 || height > 16384) return ANALYSER_ERR_INVALID_ARG;
+  const size_t part_bytes = (size_t)kMeasureBlocks * 6 * sizeof(double);
+  uint8_t* buf = nullptr;
+  if (pool_malloc(reinterpret_cast<void**>(&buf), flow_bytes + part_bytes + 6 * sizeof(double)) != cudaSuccess)
+    return ANALYSER_ERR_OOM;
+  float* flow = reinterpret_cast<float*>(buf);
+  double* d_part = reinterpret_cast<double*>(buf + flow_bytes);
+  double* d_sums = reinterpret_cast<double*>(buf + flow_bytes + part_bytes);
+  const cudaStream_t st = (cudaStream_t)stream;
+  int rc = analyser_dense_flow(fp, width, height, frame_a, frame_b, pitch_bytes, flow, stream);
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  if (rc == ANALYSER_OK) {
+    const U8Plane I{frame_a, width, height, (int)pitch_bytes}, J{frame_b, width, height, (int)pitch_bytes};
+    if (fp->fp64) flow_measure_kernel<double><<<kMeasureBlocks, kMeasureThreads, 0, st>>>(I, J, flow, d_part);
+    else flow_measure_kernel<float><<<kMeasureBlocks, kMeasureThreads, 0, st>>>(I, J, flow, d_part);
+    flow_sum_kernel<<<1, 32, 0, st>>>(d_part, kMeasureBlocks, d_sums);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s, d_sums, sizeof(s), cudaMemcpyDeviceToHost, st);
+    const cudaError_t es = cudaStreamSynchronize(st);
+    if (e != cudaSuccess || es != cudaSuccess) rc = ANALYSER_ERR_CUDA;
+  } else {
+    cudaStreamSynchronize(st);
+  }
+  pool_free(buf);
+  if (rc != ANALYSER_OK) return rc;
+  // FP64 finalisation (Sec. III.A): NCC from the sums, SWR, AMM, ACT
+  const double n = (double)width * (double)height;
+  const double c = n * s[5] - s[1] * s[2];
+  const double vi = n * s[3] - s[1] * s[1];
+  const double vj = n * s[4] - s[2] * s[2];
+  double ncc;
+  if (vi <= 0.0 && vj <= 0.0) ncc = 1.0;
+  else if (vi <= 0.0 || vj <= 0.0) ncc = 0.0;
+  else ncc = c / sqrt(vi * vj);
+  const double om = 1.0 - ncc;
+  out->ncc = ncc;
+  out->swr = om > 0.0 ? om : 0.0;
+  out->amm = s[0] / n;
+  out->act = sqrt(out->amm * out->swr);
+  for (int k = 0; k < 6; k++) out->sums[k] = s[k];
+  return ANALYSER_OK;
 }

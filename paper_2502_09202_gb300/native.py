@@ -88,6 +88,11 @@ class FlowParams(ctypes.Structure):
                 ("damp_rel", c_double), ("damp_abs", c_double)]
 
 
+class FlowMeasure(ctypes.Structure):
+    _fields_ = [("amm", c_double), ("ncc", c_double), ("swr", c_double), ("act", c_double),
+                ("sums", c_double * 6)]
+
+
 # every entry point of include/analyser.h: name -> (restype, argtypes)
 P, VP = ctypes.POINTER, ctypes.c_void_p
 SIGNATURES = {
@@ -109,6 +114,7 @@ SIGNATURES = {
     "analyser_measure_sad_sequence": (c_int, [c_int, c_int, P(c_double)]),
     "analyser_default_flow_params": (None, [P(FlowParams)]),
     "analyser_dense_flow": (c_int, [P(FlowParams), c_int, c_int, VP, VP, c_ll, VP, VP]),
+    "analyser_flow_measure": (c_int, [P(FlowParams), c_int, c_int, VP, VP, c_ll, P(FlowMeasure), VP]),
     "analyser_trim_cache": (None, []),
     "analyser_cached_bytes": (c_ll, []),
     "server_create": (c_int, [P(Params), c_ull, P(VP)]),

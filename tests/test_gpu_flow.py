@@ -130,3 +130,44 @@ def test_invalid_arguments_are_refused():
                                      None) == N.ERR_INVALID_ARG      # pitch below width
     assert N.lib.analyser_dense_flow(ctypes.byref(p), 40, 40, None, a.data_ptr(), 40, out.data_ptr(),
                                      None) == N.ERR_INVALID_ARG
+
+
+def _gpu_measure(fa, fb, **kw):
+    from paper_2502_09202_gb300 import api
+    a = torch.from_numpy(np.ascontiguousarray(fa)).cuda()
+    b = torch.from_numpy(np.ascontiguousarray(fb)).cuda()
+    return api.flow_measure(a, b, **kw)
+
+
+@pytest.mark.parametrize("t", [0, 3, 6])
+def test_flow_measures_match_the_oracle(t):
+    """AMM, NCC, SWR, ACT with the dense flow as the motion field.  FP64: the
+    flows agree within FLOW_TOL_FP64 and the sums are FP64 on both sides, so the
+    measures agree to 1e-6 (AMM, ACT) and 1e-7 (NCC); FP32: AMM within the
+    flows' mean difference bound, NCC within 2e-3."""
+    fr = _clip()
+    ref = D.flow_measure(fr[t], fr[t + 1])
+    m64 = _gpu_measure(fr[t], fr[t + 1], fp64=1)
+    assert abs(m64["amm"] - ref["amm"]) <= 1e-6 and abs(m64["act"] - ref["act"]) <= 1e-6
+    assert abs(m64["ncc"] - ref["ncc"]) <= 1e-7 and abs(m64["swr"] - ref["swr"]) <= 1e-7
+    m32 = _gpu_measure(fr[t], fr[t + 1])
+    assert abs(m32["amm"] - ref["amm"]) <= FP32_MEAN_TOL and abs(m32["ncc"] - ref["ncc"]) <= 2e-3
+    assert abs(m32["act"] - ref["act"]) <= 0.05
+
+
+@pytest.mark.parametrize("fp64", [0, 1])
+def test_flow_measure_without_flow_is_the_plain_correlation(fp64):
+    fr = _clip()
+    m = _gpu_measure(fr[1], fr[5], fp64=fp64, iters=0)
+    want = np.corrcoef(fr[1].ravel().astype(float), fr[5].ravel().astype(float))[0, 1]
+    assert m["amm"] == 0.0 and m["act"] == 0.0 and abs(m["ncc"] - want) <= 1e-9
+    m = _gpu_measure(fr[2], fr[2], fp64=fp64)
+    assert m["amm"] == 0.0 and m["act"] == 0.0 and abs(m["ncc"] - 1.0) <= 1e-12
+
+
+def test_flow_measure_is_reproducible():
+    """The FP64 sums are added in a fixed order: repeated calls agree bit for bit."""
+    fr = _clip()
+    for fp64 in (0, 1):
+        a, b = _gpu_measure(fr[0], fr[1], fp64=fp64), _gpu_measure(fr[0], fr[1], fp64=fp64)
+        assert a == b
