@@ -91,10 +91,9 @@ __device__ __forceinline__ F warp_sum(F v) {
 __device__ __forceinline__ int patch_origin(int k, int n, int S) { return min(k * S, n - kFlowPatch); }
 
 // 2x2 box mean with rounding, floor(w/2) x floor(h/2)
-__global__ void flow_down_kernel(const uint8_t* src, int sw, int spitch, uint8_t* dst, int dw, int dh, int dpitch) {
+__global__ void flow_down_kernel(const uint8_t* src, int spitch, uint8_t* dst, int dw, int dh, int dpitch) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x >= dw || y >= dh) return;
-  (void)sw;
   const uint8_t* r0 = src + (size_t)(2 * y) * spitch + 2 * x;
   const uint8_t* r1 = r0 + spitch;
   dst[(size_t)y * dpitch + x] = (uint8_t)(((unsigned)r0[0] + r0[1] + r1[0] + r1[1] + 2u) >> 2);
@@ -274,7 +273,7 @@ int dense_flow(const analyser_flow_params* fp, int width, int height, const uint
     for (int f = 0; f < 2; f++) {
       uint8_t* dst = scratch + off_img[l][f];
       const dim3 grid((w[l] + 127) / 128, h[l]);
-      flow_down_kernel<<<grid, 128, 0, st>>>(img[l - 1][f], w[l - 1], pitch[l - 1], dst, w[l], h[l], pitch[l]);
+      flow_down_kernel<<<grid, 128, 0, st>>>(img[l - 1][f], pitch[l - 1], dst, w[l], h[l], pitch[l]);
       img[l][f] = dst;
     }
     e = cudaGetLastError();
