@@ -130,13 +130,55 @@ __global__ void flow_search_kernel(U8Plane I, U8Plane J, const F* coarse, int cw
     ux = F(2) * sample_flow(coarse, cw, ch, cx, cy, 0);
     uy = F(2) * sample_flow(coarse, cw, ch, cx, cy, 1);
   }
+  const int col = lane & 7, row = lane >> 3;   // pixel 0 at (row, col), pixel 1 at (row + 4, col)
   for (int it = 0; it < iters; it++) {
     F bx = F(0), by = F(0);
+    // FP32: every pixel of the patch is sampled at the same offset u, so the
+    // 9 x 9 bilinear footprint starts at integer (x0 + floor(ux), y0 + floor(uy))
+    // with the same weights (ux - floor(ux), uy - floor(uy)) for all.  Where the
+    // footprint lies inside J (no clamping), a lane reads its two pixels'
+    // top-left values and takes the right and lower neighbours from the lanes
+    // that read them (the patch's right column and bottom row read their own).
+    // The FP64 instantiation, and FP32 elsewhere, sample each pixel at x + u as
+    // the per-pixel definition does: the two agree in exact arithmetic, but the
+    // rounding of x + u differs, and FP64 keeps the definition's rounding.
+    // (The comparisons fail for a non-finite flow, which takes the per-pixel path.)
+    const F fux = floor(ux), fuy = floor(uy);
+    const bool fast = sizeof(F) == sizeof(float) && fux >= F(-x0) && fuy >= F(-y0) &&
+                      fux <= F(J.w - 1 - kFlowPatch - x0) && fuy <= F(J.h - 1 - kFlowPatch - y0);
+    if (fast) {   // warp-uniform
+      const int ix = x0 + (int)fux, iy = y0 + (int)fuy;
+      const F fx = ux - fux, fy = uy - fuy;
+      const uint8_t* q = J.p + (size_t)(iy + row) * J.pitch + ix + col;
+      const size_t p4 = (size_t)4 * J.pitch;
+      const int a = q[0], b = q[p4];   // J(iy + row, ix + col), J(iy + row + 4, ix + col)
+      int ar = __shfl_sync(0xFFFFFFFFu, a, lane + 1), br = __shfl_sync(0xFFFFFFFFu, b, lane + 1);
+      if (col == 7) {
+        ar = q[1];
+        br = q[p4 + 1];
+      }
+      // the row below pixel 0: lane + 8's pixel 0 (row < 3) or column col's pixel 1 (row 3)
+      const int sa = __shfl_sync(0xFFFFFFFFu, a, lane + 8), sar = __shfl_sync(0xFFFFFFFFu, ar, lane + 8);
+      const int sb = __shfl_sync(0xFFFFFFFFu, b, col), sbr = __shfl_sync(0xFFFFFFFFu, br, col);
+      const int ad = row < 3 ? sa : sb, adr = row < 3 ? sar : sbr;
+      // the row below pixel 1: lane + 8's pixel 1 (row < 3) or row iy + 8 (row 3)
+      int bd = __shfl_sync(0xFFFFFFFFu, b, lane + 8), bdr = __shfl_sync(0xFFFFFFFFu, br, lane + 8);
+      if (row == 3) {   // q is on row iy + 3; the footprint's last row is iy + 8
+        bd = q[(size_t)5 * J.pitch];
+        bdr = q[(size_t)5 * J.pitch + 1];
+      }
+      const F v0 = (F(a) * (F(1) - fx) + F(ar) * fx) * (F(1) - fy) + (F(ad) * (F(1) - fx) + F(adr) * fx) * fy;
+      const F v1 = (F(b) * (F(1) - fx) + F(br) * fx) * (F(1) - fy) + (F(bd) * (F(1) - fx) + F(bdr) * fx) * fy;
+      const F r0 = v0 - t[0], r1 = v1 - t[1];
+      bx = gx[0] * r0 + gx[1] * r1;
+      by = gy[0] * r0 + gy[1] * r1;
+    } else {
 #pragma unroll
-    for (int k = 0; k < 2; k++) {
-      const F r = sample_u8(J, X[k] + ux, Y[k] + uy) - t[k];
-      bx += gx[k] * r;
-      by += gy[k] * r;
+      for (int k = 0; k < 2; k++) {
+        const F r = sample_u8(J, X[k] + ux, Y[k] + uy) - t[k];
+        bx += gx[k] * r;
+        by += gy[k] * r;
+      }
     }
     bx = warp_sum(bx);
     by = warp_sum(by);
