@@ -391,6 +391,22 @@ def test_served_requests_match_the_oracle():
     srv.close()
 
 
+def test_batched_clips_match_the_oracle():
+    """Three clips drawn as in the batched workload (mixed structures and
+    lengths, two sizes) analysed together by one server (one tile shape for
+    all, one coarse and one refinement launch per wave): every result equals
+    the oracle's analysis of the same clip, value by value."""
+    api = _api()
+    specs = synth.config_batched(nclips=3, length_range=(60, 90), resolutions=((320, 180), (640, 360)))
+    clips = [synth.Clip(s).frames() for s in specs]
+    srv = api.Server(budget_bytes=8 << 30)
+    tickets = [srv.submit(f, s.fps) for s, f in zip(specs, clips)]
+    srv.drain()
+    for t, f in zip(tickets, clips):
+        _compare_results(srv.poll(t), OA.analyse_frames(f))
+    srv.close()
+
+
 def test_packed_sequence_rates_are_measured():
     """Each packed |a-b| sequence of the peak loop runs and gives a positive
     rate; sequence 0 is analyser_measure_sad_peak's; a sequence outside 0..4 is
