@@ -182,8 +182,6 @@ def _peaks():
         return {}
 
 
-
-
 def cpu_baseline(spec, nframes_sample: int = 16, start: int = 300):
     """The oracle as it stands on this host's cores: a bounded sample of the clip
     (always-on pairs over a spawn-started pool, then the sequential detectors)."""
@@ -297,9 +295,18 @@ def run_flow(args):
         res["fp64" if fp64 else "fp32"] = {"ms_per_pair": ms, "pairs_per_s": 1000.0 / ms,
                                             "search_gflop_per_s": flops / (ms * 1e-3) / 1e9, "pairs": k,
                                             "measure_ms_per_pair": ms_m}
+    # FP32 peak from the unit counts: SMs x 128 FP32 lanes x 2 (multiply-add) x
+    # the maximum SM clock the driver measured (2070 MHz when not recorded)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = _peaks().get("sm_max_mhz") or 2070.0
+    peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    got = res["fp32"]["search_gflop_per_s"] / 1e3
     print(json.dumps({"mode": "flow", "workload": f"{W}x{H} frame pairs of {WORKLOAD}", "params": {
         "levels": p.levels, "patch": p.patch, "stride": p.stride, "iters": p.iters, "damp_rel": p.damp_rel,
-        "damp_abs": p.damp_abs}, "search_pixel_steps_per_pair": steps_px, "results": res}))
+        "damp_abs": p.damp_abs}, "search_pixel_steps_per_pair": steps_px, "results": res,
+        "roofline": {"bound": "l1 (bilinear gathers of the search kernel)", "achieved": got, "peak": peak,
+                     "unit": "TFLOP/s (FP32, 14 operations per pixel-step over the whole flow call)",
+                     "frac": got / peak, "peak_source": f"derived: {sms} SMs x 128 lanes x 2 x {mhz:.0f} MHz"}}))
     return 0
 
 
