@@ -658,7 +658,11 @@ def run_gpu(args):
                    "param_overrides": args.overrides},
         "e2e": {"value": e2e_value, "unit": "frames/s", "ms_per_step": ms_e2e,
                 "h2d_bytes_per_step": int(hprofs[-1]["h2d_bytes"]), "d2h_bytes_per_step": int(hprofs[-1]["d2h_bytes"]),
-                "h2d_link_gbs": link_gbs, "host_step_ms": host_step_ms},
+                "h2d_link_gbs": link_gbs, "host_step_ms": host_step_ms,
+                # beside the mean over all steps (the value above): the median step,
+                # which isolated host-side stalls of single steps do not move
+                "median_step_ms": statistics.median(host_step_ms),
+                "value_at_median_step": job_throughput(world, T, statistics.median(host_step_ms))},
         "step_ms": dev_step_ms,
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": "pair_kernel", "achieved": achieved, "peak": sad_peak,
